@@ -1,0 +1,224 @@
+"""Seeded synthetic inputs for the subspace multicoil NUFFT operator.
+
+The paper's in-vivo dataset (a whole-brain 3D spiral MRF scan, 8 coils, Sec. 3.1)
+is not available, so every input here is synthetic with the shapes and structure
+of that acquisition: a smooth complex time-compressed image series (TSMI,
+Sec. 2 after Eq. 1), smooth coil sensitivities, golden-angle-rotated 3D spiral
+arms (one or more per frame), and an orthonormal temporal subspace basis V.
+
+This module holds no NUFFT arithmetic: it only draws inputs.  Both the FP64
+oracle tests and the CUDA path consume these arrays unchanged.
+
+Layouts (C order, complex64 unless stated):
+  x      [K][N1][N2][N3]      TSMI, K subspace channels
+  S      [C][N1][N2][N3]      coil sensitivities
+  omega  [J][3] float32       k-space locations in radians, |omega_d| <= pi,
+                              omega[:, d] pairs with image axis d
+  frame  [J] int32            frame index t of each sample (frames are contiguous)
+  V      [T][K]               temporal subspace basis
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Seeds of the independent input streams.
+SEED_PHANTOM = 0
+SEED_V = 2
+SEED_NOISE = 3
+SEED_COILS_DRAW = 4
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """Shape of one synthetic reconstruction problem."""
+
+    name: str
+    n: tuple            # image matrix (N1, N2, N3)
+    K: int              # subspace rank
+    C: int              # coils
+    T: int              # frames
+    arms: int           # spiral arms per frame
+    arm_len: int        # samples per arm
+    width: int          # Kaiser-Bessel kernel width W
+    oversamp: float     # grid oversampling sigma
+    batch: int          # coil minibatch per operator call
+
+    @property
+    def samples_per_frame(self) -> int:
+        return self.arms * self.arm_len
+
+    @property
+    def J(self) -> int:
+        return self.T * self.samples_per_frame
+
+    @property
+    def nvox(self) -> int:
+        return int(np.prod(self.n))
+
+
+# Workloads named by what they are.  The 128^3 one is the single-GPU throughput
+# workload; the 32^3 one is small enough for the FP64 oracle to finish in seconds.
+WORKLOADS = {
+    "vol32_w6": Workload("vol32_w6", (32, 32, 32), 5, 4, 100, 1, 512, 6, 2.0, 4),
+    "vol128_w4": Workload("vol128_w4", (128, 128, 128), 5, 8, 480, 1, 1024, 4, 1.25, 2),
+    "vol200_w4": Workload("vol200_w4", (200, 200, 160), 5, 32, 1000, 2, 1024, 4, 1.25, 8),
+    "vol24_w6": Workload("vol24_w6", (24, 24, 24), 5, 4, 100, 1, 512, 6, 2.0, 2),
+}
+
+
+def golden_means_3d():
+    """Multidimensional golden means for 3D direction sampling.
+
+    They are 1/lam and 1/lam^2 for the real root lam of lam^3 = lam^2 + 1
+    (Chan et al. 2009, the 3D generalisation of the golden ratio).
+    """
+    lam = 1.0
+    for _ in range(60):  # Newton on f(l) = l^3 - l^2 - 1
+        f = lam ** 3 - lam ** 2 - 1.0
+        lam -= f / (3 * lam ** 2 - 2 * lam)
+    return 1.0 / lam ** 2, 1.0 / lam  # (~0.4656, ~0.6823)
+
+
+def spiral_trajectory(T: int, arms: int, arm_len: int, dtype=np.float32):
+    """Golden-angle-rotated planar Archimedean spiral arms in 3D k-space.
+
+    Arm i = t*arms + a.  Radius r(s) = pi * s / (arm_len - 1) and angle
+    theta(s) = 2*pi*(arm_len/64)*s/(arm_len - 1) (arm_len/64 turns per arm).  The
+    plane normal of arm i follows the 3D golden means and the arm is turned
+    in-plane by the golden angle pi*(3 - sqrt 5)*i.  |k| <= pi everywhere.
+
+    Returns (omega [T*arms*arm_len][3] float32, frame [J] int32).
+    """
+    phi1, phi2 = golden_means_3d()
+    n_arms = T * arms
+    i = np.arange(n_arms, dtype=np.float64)
+    cz = 2.0 * np.mod(i * phi1, 1.0) - 1.0
+    az = 2.0 * np.pi * np.mod(i * phi2, 1.0)
+    sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+    nrm = np.stack([sz * np.cos(az), sz * np.sin(az), cz], axis=1)
+    # orthonormal in-plane basis (e1, e2) perpendicular to the normal
+    ref = np.where(np.abs(nrm[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    e1 = np.cross(nrm, ref)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(nrm, e1)
+    s = np.arange(arm_len, dtype=np.float64) / max(arm_len - 1, 1)
+    r = np.pi * s
+    theta = 2.0 * np.pi * (arm_len / 64.0) * s
+    psi = np.pi * (3.0 - math.sqrt(5.0)) * i
+    ang = theta[None, :] + psi[:, None]                     # [n_arms][arm_len]
+    k = (r[None, :, None] * (np.cos(ang)[:, :, None] * e1[:, None, :]
+                             + np.sin(ang)[:, :, None] * e2[:, None, :]))
+    omega = k.reshape(-1, 3)
+    omega = np.clip(omega, -np.pi, np.pi).astype(dtype)
+    frame = np.repeat(np.arange(T, dtype=np.int32), arms * arm_len)
+    return omega, frame
+
+
+def _smooth_fft(vol: np.ndarray, sigma_vox: float) -> np.ndarray:
+    """Gaussian smoothing (periodic) of the last three axes by FFT multiplication."""
+    shp = vol.shape[-3:]
+    f = np.fft.fftn(vol, axes=(-3, -2, -1))
+    g = np.ones(shp)
+    for d, nd in enumerate(shp):
+        fr = np.fft.fftfreq(nd)
+        gd = np.exp(-2.0 * (np.pi * sigma_vox * fr) ** 2)
+        sh = [1, 1, 1]
+        sh[d] = nd
+        g = g * gd.reshape(sh)
+    return np.fft.ifftn(f * g, axes=(-3, -2, -1))
+
+
+def _centred_coords(n):
+    """Normalised coordinates in [-1, 1) along each axis (FOV/2 units)."""
+    return [(np.arange(nd) - nd // 2) / (nd / 2.0) for nd in n]
+
+
+def ellipsoid_phantom(n, K: int, seed: int = SEED_PHANTOM, n_ell: int = 12, dtype=np.complex64):
+    """Sum of random ellipsoids with complex per-channel amplitudes, smoothed.
+
+    Centres ~ U(-0.6, 0.6), semi-axes ~ U(0.1, 0.45) (FOV/2 units), random
+    rotation, amplitude of ellipsoid e in channel k ~ CN(0,1)/(k+1); the sum is
+    smoothed with a Gaussian of one voxel.  Returns x [K][N1][N2][N3].
+    """
+    rng = np.random.default_rng(seed)
+    c1, c2, c3 = _centred_coords(n)
+    X, Y, Z = np.meshgrid(c1, c2, c3, indexing="ij")
+    P = np.stack([X, Y, Z], axis=-1)
+    x = np.zeros((K,) + tuple(n), dtype=np.complex128)
+    for _ in range(n_ell):
+        ctr = rng.uniform(-0.6, 0.6, size=3)
+        ax = rng.uniform(0.1, 0.45, size=3)
+        q, _r = np.linalg.qr(rng.standard_normal((3, 3)))
+        amp = (rng.standard_normal(K) + 1j * rng.standard_normal(K)) / np.sqrt(2.0)
+        amp = amp / (np.arange(K) + 1.0)
+        loc = (P - ctr) @ q
+        inside = np.sum((loc / ax) ** 2, axis=-1) <= 1.0
+        x[:, inside] += amp[:, None]
+    x = _smooth_fft(x, 1.0)
+    return x.astype(dtype)
+
+
+def coil_maps(n, C: int, dtype=np.complex64):
+    """Smooth Gaussian-bump coil sensitivities normalised to unit root-sum-of-squares.
+
+    Coil c sits at a Fibonacci-sphere direction at radius 1.2 (FOV/2 units); its
+    magnitude is a Gaussian with standard deviation 0.6 FOV and its phase is 2*pi*c/C plus a small
+    linear ramp.  Returns S [C][N1][N2][N3].
+    """
+    c1, c2, c3 = _centred_coords(n)
+    X, Y, Z = np.meshgrid(c1, c2, c3, indexing="ij")
+    S = np.empty((C,) + tuple(n), dtype=np.complex128)
+    ga = np.pi * (3.0 - math.sqrt(5.0))
+    for c in range(C):
+        zc = 1.0 - 2.0 * (c + 0.5) / C
+        rc = math.sqrt(max(0.0, 1.0 - zc * zc))
+        d = np.array([rc * math.cos(ga * c), rc * math.sin(ga * c), zc]) * 1.2
+        dist2 = (X - d[0]) ** 2 + (Y - d[1]) ** 2 + (Z - d[2]) ** 2
+        mag = np.exp(-dist2 / (2.0 * 1.2 ** 2))  # std 0.6 FOV = 1.2 in FOV/2 units
+        ramp = 0.3 * (d[0] * X + d[1] * Y + d[2] * Z)
+        S[c] = mag * np.exp(1j * (2.0 * np.pi * c / C + ramp))
+    rss = np.sqrt(np.sum(np.abs(S) ** 2, axis=0))
+    S /= rss[None]
+    return S.astype(dtype)
+
+
+def subspace_basis(T: int, K: int, seed: int = SEED_V, real: bool = False, dtype=np.complex64):
+    """Orthonormal T x K basis: Q of the reduced QR of a seeded Gaussian matrix."""
+    rng = np.random.default_rng(seed)
+    if real:
+        g = rng.standard_normal((T, K))
+    else:
+        g = rng.standard_normal((T, K)) + 1j * rng.standard_normal((T, K))
+    q, _ = np.linalg.qr(g)
+    return q.astype(dtype)
+
+
+def coil_minibatches(C: int, B: int, steps: int, seed: int = SEED_COILS_DRAW):
+    """Coil minibatches of size B drawn uniformly without replacement per call."""
+    rng = np.random.default_rng(seed)
+    return [np.sort(rng.choice(C, size=B, replace=False)).astype(np.int32) for _ in range(steps)]
+
+
+def complex_noise(shape, sigma: float, seed: int = SEED_NOISE, dtype=np.complex64):
+    """Circular complex Gaussian noise with per-component std sigma/sqrt(2)."""
+    rng = np.random.default_rng(seed)
+    z = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * (sigma / math.sqrt(2.0))
+    return z.astype(dtype)
+
+
+def random_complex(shape, seed: int, dtype=np.complex64):
+    """Unstructured complex Gaussian array (for adjoint-identity and linearity cases)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(dtype)
+
+
+def make_problem(w: Workload, seed: int = SEED_PHANTOM):
+    """All per-trajectory inputs of a workload: (x, S, V, omega, frame)."""
+    x = ellipsoid_phantom(w.n, w.K, seed=seed)
+    S = coil_maps(w.n, w.C)
+    V = subspace_basis(w.T, w.K)
+    omega, frame = spiral_trajectory(w.T, w.arms, w.arm_len)
+    return x, S, V, omega, frame
