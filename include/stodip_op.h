@@ -1,0 +1,194 @@
+/*
+ * stodip_op.h -- C ABI of the GB300 (sm_103a) subspace multicoil NUFFT operator.
+ *
+ * StoDIP (arXiv 2408.02367), Sec. 2, Eq. 1: the acquisition operator A maps a
+ * time-compressed image series x in C^{N x K} to multicoil non-Cartesian
+ * k-space and "includes coil sensitivities, NUFFT and temporal SVD".  Sec. 2.1,
+ * Eq. 3 splits it per coil, A = {A_c}, and Algorithm 1 applies one A_c (or a
+ * minibatch of them) and its adjoint (through loss.backward()) per iteration.
+ *
+ * For a sample j of frame t_j at k-space location omega_j (radians):
+ *
+ *   A_c(x)[j] = sum_n exp(-i omega_j . n) S_c[n] sum_k V[t_j, k] x_k[n]
+ *
+ * with centred voxel indices n_d = i_d - floor(N_d / 2) (storage offset i_d).
+ * The library evaluates this by Kaiser-Bessel gridding on a sigma-oversampled
+ * grid of width-W kernels (Jackson et al. 1991; beta of Beatty et al. 2005):
+ * deapodise and multiply by S_c, 3D FFT, interpolate W^3 taps contracting the K
+ * channels with V[t_j, :].  The adjoint is the exact conjugate transpose of those
+ * steps and sums over the coil minibatch (the gradient of sum_c L_c, Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Complex values are interleaved float32 pairs (complex64), C order.
+ *   - Every call returns an int status (SDP_OK = 0).  Nothing throws or aborts
+ *     across the ABI.  Arguments are checked on the host before any launch;
+ *     device-side faults of the data (a coil index out of range) are recorded in
+ *     the plan's device status word and reported by sdp_status().
+ *   - Pointers marked DEVICE must be CUDA device pointers on the plan's device;
+ *     HOST pointers are ordinary host memory.  The caller owns every pointer it
+ *     passes; the plan owns its own copies of V, S, the sorted trajectory, the
+ *     bin tables and the workspace.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *     sdp_forward / sdp_adjoint and their variants are asynchronous, allocate
+ *     nothing and do not synchronise, so they can be captured in a CUDA graph.
+ *   - Calls on one plan share its workspace: calls that overlap in time on
+ *     different streams race.  Serialise them on one stream.
+ */
+#ifndef STODIP_OP_H
+#define STODIP_OP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SDP_OK 0
+#define SDP_ERR_INVALID_ARG 1   /* bad pointer, size or parameter (checked on the host) */
+#define SDP_ERR_OOM 2           /* device allocation failed in sdp_plan_create */
+#define SDP_ERR_CUDA 3          /* a CUDA runtime call failed */
+#define SDP_ERR_TIMEOUT 4       /* a bounded device wait gave up */
+#define SDP_ERR_BOUNDS 5        /* device-side index check failed (coil index) */
+#define SDP_ERR_UNSUPPORTED 6   /* parameters outside the supported range */
+
+/* Plan flags (bit mask). */
+#define SDP_FLAG_NONE 0u
+
+/* Opaque plan, owned by the library. */
+typedef struct sdp_plan_s* sdp_plan_t;
+
+/*
+ * Description of one operator (one trajectory, one image matrix).
+ *   n[3]           image matrix N1, N2, N3 (axis 3 contiguous), each >= 2.
+ *   oversamp       grid oversampling sigma in [1, 4]; the grid length along axis d
+ *                  is the smallest even 2,3,5-smooth M_d >= max(ceil(sigma N_d), 2W).
+ *   width          Kaiser-Bessel kernel width W in taps, 2..8.
+ *   K              subspace rank (channels of x), 1..16.
+ *   T              frames (rows of V), >= 1.
+ *   C              coils (rows of coil_maps), >= 1.
+ *   J              samples per coil (all frames), >= 1 and < 2^31.
+ *   max_batch      largest coil minibatch B of any later call, 1..64; the
+ *                  workspace is sized for it.
+ *   frame_offsets  HOST int64 [T+1]: samples of frame t are [off[t], off[t+1]),
+ *                  off[0] = 0, off[T] = J, non-decreasing.  Read during create only.
+ *   traj           DEVICE float32 [J][3], omega in radians, |omega_d| <= pi;
+ *                  omega[:, d] pairs with image axis d.  Read during create only.
+ *   V              DEVICE complex64 [T][K] temporal subspace basis, copied.
+ *   coil_maps      DEVICE complex64 [C][N1][N2][N3] coil sensitivities S_c, copied.
+ */
+typedef struct {
+    int64_t n[3];
+    double oversamp;
+    int32_t width;
+    int32_t K;
+    int32_t T;
+    int32_t C;
+    int64_t J;
+    int32_t max_batch;
+    uint32_t flags;
+    const int64_t* frame_offsets;
+    const float* traj;
+    const void* V;
+    const void* coil_maps;
+} sdp_plan_desc;
+
+/*
+ * Build a plan: grid sizes, Kaiser-Bessel beta and deapodisation tables, FFT
+ * twiddles (float64 on the host, stored as float32), grid coordinates of every
+ * sample, the bin sort of the samples and the bin incidence lists of the
+ * adjoint, copies of V and S, and a workspace for max_batch coils.
+ * Allocates device memory and synchronises `stream`; not capturable.
+ * On success *out holds the plan; on failure *out is NULL and nothing leaks.
+ */
+int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
+
+/* Release every resource of the plan (NULL is a no-op).  Synchronises the device. */
+void sdp_plan_destroy(sdp_plan_t plan);
+
+/*
+ * Forward operator on a coil minibatch (Eq. 1 / Eq. 3, Algorithm 1 line 4):
+ *   y[b][j] = A_{coil_idx[b]}(x)[j]   for b < B, j < J.
+ *   x         DEVICE complex64 [K][N1][N2][N3]
+ *   coil_idx  DEVICE int32 [B], each in [0, C); duplicates allowed.  Read by the
+ *             kernels, so a captured graph sees the values present at replay.
+ *   B         1..max_batch
+ *   y         DEVICE complex64 [B][J] (overwritten)
+ */
+int sdp_forward(sdp_plan_t plan, const void* x, const int32_t* coil_idx, int32_t B,
+                void* y, void* stream);
+
+/*
+ * Adjoint on a coil minibatch, summed over it (the gradient of
+ * sum_{b} L_{c_b}, Eq. 3, as used by loss.backward() in Algorithm 1):
+ *   out_k = (accumulate ? out_k : 0) + sum_b A_{coil_idx[b]}^H (y[b])   (channel k)
+ *   y         DEVICE complex64 [B][J]
+ *   coil_idx  DEVICE int32 [B] as in sdp_forward
+ *   out       DEVICE complex64 [K][N1][N2][N3]
+ *   accumulate 0 = overwrite, 1 = add into out
+ */
+int sdp_adjoint(sdp_plan_t plan, const void* y, const int32_t* coil_idx, int32_t B,
+                void* out, int32_t accumulate, void* stream);
+
+/*
+ * Channel-range forms of the two calls (the building block of the plain
+ * one-coil-one-channel-per-launch form, and of callers that split K):
+ *   forward: y[b] = (accumulate ? y[b] : 0) + sum_{k0 <= k < k0+nk} V[t_j,k] NUFFT(S_c x_k)
+ *   adjoint: out_k (+)= sum_b A^H restricted to channel k, for k0 <= k < k0+nk only;
+ *            other channels of out are not touched.
+ *   0 <= k0, 1 <= nk, k0 + nk <= K.
+ */
+int sdp_forward_channels(sdp_plan_t plan, const void* x, const int32_t* coil_idx, int32_t B,
+                         int32_t k0, int32_t nk, void* y, int32_t accumulate, void* stream);
+int sdp_adjoint_channels(sdp_plan_t plan, const void* y, const int32_t* coil_idx, int32_t B,
+                         int32_t k0, int32_t nk, void* out, int32_t accumulate, void* stream);
+
+/*
+ * Synchronise `stream`, return the plan's device status word (SDP_OK or the
+ * first device-side error recorded since the last call) and clear it.
+ */
+int sdp_status(sdp_plan_t plan, void* stream);
+
+/*
+ * Plan facts for callers and tests.  Writes min(cap, 16) int64 values:
+ *   [0..2] grid M1, M2, M3   [3] J   [4] K   [5] max_batch
+ *   [6..8] spread bin sizes  [9] number of bins  [10] number of spread subproblems
+ *   [11] incidences (sample, bin) of the adjoint  [12] workspace bytes
+ *   [13] plan-owned device bytes in total  [14] width W  [15] C
+ * Returns SDP_OK or SDP_ERR_INVALID_ARG.
+ */
+int sdp_plan_info(sdp_plan_t plan, int64_t* out, int32_t cap);
+
+/* Kaiser-Bessel beta the plan uses (Beatty et al. 2005), or -1 for a NULL plan. */
+double sdp_plan_beta(sdp_plan_t plan);
+
+/* Bytes of device workspace the plan holds for its max_batch (0 for NULL). */
+size_t sdp_workspace_bytes(sdp_plan_t plan);
+
+/* Kernels launched by this library in this process so far (all plans). */
+int64_t sdp_launch_count(void);
+
+/*
+ * Per-stage timing with CUDA events on the launching stream.
+ * sdp_profile_enable(plan, 1) brackets every later launch of the plan with a
+ * pair of events (recorded on the launch's own stream); sdp_profile_read
+ * synchronises those events, adds each launch's duration to its stage and
+ * writes up to `cap` stages: ms[s] = summed milliseconds, launches[s] = count.
+ * Stages: 0 prologue+FFT axis 3, 1 FFT axis 2, 2 FFT axis 1, 3 interpolation,
+ * 4 spread, 5 inverse FFT axis 1, 6 inverse FFT axis 2, 7 inverse FFT axis 3
+ * + epilogue.  Reading resets the sums.  Returns the number of stages written
+ * or a negative status.  Profiling is off by default and costs two event
+ * records per launch when on.
+ */
+int sdp_profile_enable(sdp_plan_t plan, int32_t enable);
+int sdp_profile_read(sdp_plan_t plan, double* ms, int64_t* launches, int32_t cap);
+
+/* Static text for a status code. */
+const char* sdp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STODIP_OP_H */

@@ -1,0 +1,626 @@
+// C ABI of the subspace multicoil NUFFT operator (declared in include/stodip_op.h):
+// plan construction on the host (grid sizes, Kaiser-Bessel beta and
+// deapodisation, FFT factorisation and twiddles, grid coordinates, bin sort,
+// spread incidence lists), and the launch sequences of the forward operator
+// A_c and its adjoint (StoDIP Sec. 2 Eq. 1, Sec. 2.1 Eq. 3, Algorithm 1).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sdp_internal.cuh"
+
+using namespace sdp;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+std::atomic<long long> g_launches{0};
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct sdp_plan_s {
+    int dev = 0;
+    Geo geo{};
+    int64_t n[3] = {0, 0, 0};
+    int64_t M[3] = {0, 0, 0};
+    double sigma = 0, beta = 0;
+    int maxB = 0;
+    uint32_t flags = 0;
+    FftAxis ax[3]{};
+    int bs[3] = {0, 0, 0};
+    int nb[3] = {0, 0, 0};
+    int nbins = 0;
+    int nsub = 0;
+    long long ninc = 0;
+    long long slots_per_b = 0;
+    // device memory
+    float4* pts = nullptr;
+    int* tframe = nullptr;
+    float2* V = nullptr;
+    float2* S = nullptr;
+    float* dinv = nullptr;   // [N1 | N2 | N3]
+    float2* tw = nullptr;    // [M1 | M2 | M3]
+    int* inc = nullptr;
+    SubProb* subs = nullptr;
+    float2* partials = nullptr;
+    int* counters = nullptr;
+    int* status = nullptr;
+    float2* bufA = nullptr;
+    float2* bufB = nullptr;
+    size_t workspace_bytes = 0;
+    size_t total_bytes = 0;
+    std::vector<void*> allocs;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> prof_used;
+    std::vector<ProfRec> prof_free;
+    double prof_ms[kNumStages] = {0};
+    long long prof_n[kNumStages] = {0};
+};
+
+namespace {
+
+bool smooth235(long long m) {
+    for (int p : {2, 3, 5})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+long long grid_len(long long n, double sigma, int W) {
+    long long m = std::max((long long)std::ceil(sigma * (double)n), 2LL * W);
+    while ((m % 2) || !smooth235(m)) ++m;
+    return m;
+}
+
+double i0(double x) { return std::cyl_bessel_i(0.0, x); }
+
+// Continuous Fourier transform of the normalised Kaiser-Bessel window.
+double kb_ft(double xi, int W, double beta) {
+    const double z2 = beta * beta - (kPi * W * xi) * (kPi * W * xi);
+    const double z = std::sqrt(std::fabs(z2));
+    double v;
+    if (z == 0.0)
+        v = 1.0;
+    else if (z2 > 0)
+        v = std::sinh(z) / z;
+    else
+        v = std::sin(z) / z;
+    return W * v / i0(beta);
+}
+
+template <typename T>
+int dev_alloc(sdp_plan_s* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return SDP_ERR_OOM;
+    }
+    p->allocs.push_back(q);
+    p->total_bytes += count * sizeof(T);
+    *ptr = static_cast<T*>(q);
+    return SDP_OK;
+}
+
+void free_plan(sdp_plan_s* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    for (void* q : p->allocs) cudaFree(q);
+    for (auto& r : p->prof_used) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto& r : p->prof_free) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete p;
+}
+
+#define SDP_TRY(expr)                      \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != SDP_OK) return _rc;     \
+    } while (0)
+
+#define SDP_CUDA(expr)                     \
+    do {                                   \
+        if ((expr) != cudaSuccess) {       \
+            cudaGetLastError();            \
+            return SDP_ERR_CUDA;           \
+        }                                  \
+    } while (0)
+
+// Grid coordinate of one axis, bit-for-bit the definition of the oracle:
+// g = omega * (M / 2 pi) in float64, wrapped into [0, M), rounded to float32,
+// a float32 equal to M becomes 0.  (Built with -ffp-contract=off.)
+float grid_coord(float omega, long long M) {
+    const double m = (double)M;
+    const double s = m / (2.0 * kPi);
+    double g = (double)omega * s;
+    if (g < 0.0) g = g + m;
+    if (g >= m) g = g - m;
+    float g32 = (float)g;
+    if (g32 >= (float)m) g32 = 0.0f;
+    return g32;
+}
+
+int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
+    const int W = d->width;
+    const int K = d->K;
+    const long long J = d->J;
+    for (int a = 0; a < 3; ++a) {
+        p->n[a] = d->n[a];
+        p->M[a] = grid_len(d->n[a], d->oversamp, W);
+        if (p->M[a] > (1 << 14)) return SDP_ERR_UNSUPPORTED;
+    }
+    const long long G = p->M[0] * p->M[1] * p->M[2];
+    const long long nvox = p->n[0] * p->n[1] * p->n[2];
+    if (G >= (1LL << 31) || nvox >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
+    p->sigma = d->oversamp;
+    const double arg = (W / d->oversamp) * (W / d->oversamp) * (d->oversamp - 0.5) * (d->oversamp - 0.5) - 0.8;
+    if (!(arg > 0)) return SDP_ERR_UNSUPPORTED;
+    p->beta = kPi * std::sqrt(arg);
+    p->maxB = d->max_batch;
+    p->flags = d->flags;
+    Geo& g = p->geo;
+    for (int a = 0; a < 3; ++a) {
+        g.N[a] = (int)p->n[a];
+        g.M[a] = (int)p->M[a];
+    }
+    g.W = W;
+    g.K = K;
+    g.T = d->T;
+    g.C = d->C;
+    g.J = (int)J;
+    g.beta = (float)p->beta;
+    g.inv_i0_beta = (float)(1.0 / i0(p->beta));
+    g.halfW = (float)(0.5 * W);
+    for (int a = 0; a < 3; ++a)
+        if (!fft_factor(g.M[a], &p->ax[a])) return SDP_ERR_UNSUPPORTED;
+
+    // ---- host tables ----
+    std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
+    {
+        size_t o = 0;
+        for (int a = 0; a < 3; ++a)
+            for (long long i = 0; i < p->n[a]; ++i) {
+                const double nc = (double)(i - p->n[a] / 2);
+                dinv[o++] = (float)(1.0 / kb_ft(nc / (double)p->M[a], W, p->beta));
+            }
+    }
+    std::vector<float2> tw;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<float2> t = fft_twiddles(g.M[a]);
+        tw.insert(tw.end(), t.begin(), t.end());
+    }
+
+    // ---- trajectory -> grid coordinates, frames ----
+    std::vector<float> traj((size_t)J * 3);
+    SDP_CUDA(cudaMemcpyAsync(traj.data(), d->traj, traj.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SDP_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> frame((size_t)J);
+    for (int t = 0; t < d->T; ++t)
+        for (long long j = d->frame_offsets[t]; j < d->frame_offsets[t + 1]; ++j) frame[j] = t;
+    std::vector<float> gc((size_t)J * 3);
+    for (long long j = 0; j < J; ++j) {
+        const float* om = &traj[(size_t)j * 3];
+        if (!(std::fabs(om[0]) <= (float)kPi + 1e-6f && std::fabs(om[1]) <= (float)kPi + 1e-6f &&
+              std::fabs(om[2]) <= (float)kPi + 1e-6f))
+            return SDP_ERR_INVALID_ARG;
+        for (int a = 0; a < 3; ++a) gc[(size_t)j * 3 + a] = grid_coord(om[a], p->M[a]);
+    }
+
+    // ---- bins: shape chosen so that a K-channel tile fits in 48 KB of shared memory ----
+    int bs[3] = {8, 8, 16};
+    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[2] > 4) bs[2] /= 2;
+    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[1] > 4) bs[1] /= 2;
+    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[0] > 4) bs[0] /= 2;
+    for (int a = 0; a < 3; ++a) {
+        p->bs[a] = bs[a];
+        p->nb[a] = (int)((p->M[a] + bs[a] - 1) / bs[a]);
+    }
+    const long long nbins = (long long)p->nb[0] * p->nb[1] * p->nb[2];
+    if (nbins >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
+    p->nbins = (int)nbins;
+
+    // window start and the bin of each sample (bin of the sample's own coordinate)
+    const float halfW = (float)(0.5 * W);
+    std::vector<int> m0((size_t)J * 3);
+    std::vector<long long> sbin((size_t)J);
+    for (long long j = 0; j < J; ++j) {
+        long long bi = 0;
+        for (int a = 0; a < 3; ++a) {
+            const float gv = gc[(size_t)j * 3 + a];
+            const float tt = gv - halfW;
+            m0[(size_t)j * 3 + a] = (int)std::ceil(tt);
+            int ba = (int)(gv / (float)bs[a]);
+            if (ba >= p->nb[a]) ba = p->nb[a] - 1;
+            bi = bi * p->nb[a] + ba;
+        }
+        sbin[j] = bi;
+    }
+    // stable counting sort of samples by bin
+    std::vector<long long> cnt(nbins + 1, 0);
+    for (long long j = 0; j < J; ++j) cnt[sbin[j] + 1]++;
+    for (long long b = 0; b < nbins; ++b) cnt[b + 1] += cnt[b];
+    std::vector<int> perm((size_t)J);   // sorted position -> original sample
+    {
+        std::vector<long long> cur(cnt.begin(), cnt.end() - 1);
+        for (long long j = 0; j < J; ++j) perm[cur[sbin[j]]++] = (int)j;
+    }
+    std::vector<float4> pts((size_t)J);
+    std::vector<int> tf((size_t)J);
+    for (long long s = 0; s < J; ++s) {
+        const int j = perm[s];
+        float4 q;
+        q.x = gc[(size_t)j * 3 + 0];
+        q.y = gc[(size_t)j * 3 + 1];
+        q.z = gc[(size_t)j * 3 + 2];
+        int jj = j;
+        std::memcpy(&q.w, &jj, sizeof(int));
+        pts[s] = q;
+        tf[s] = frame[j];
+    }
+
+    // incidences: (bin, sorted sample) for every bin a window touches
+    auto window_bins = [&](int m0a, int a, int* out) {
+        int nbs = 0;
+        for (int t = 0; t < W; ++t) {
+            long long pos = m0a + t;
+            if (pos < 0) pos += p->M[a];
+            if (pos >= p->M[a]) pos -= p->M[a];
+            const int b = (int)(pos / bs[a]);
+            bool seen = false;
+            for (int q = 0; q < nbs; ++q) seen |= (out[q] == b);
+            if (!seen) out[nbs++] = b;
+        }
+        return nbs;
+    };
+    std::vector<long long> icnt(nbins + 1, 0);
+    for (long long s = 0; s < J; ++s) {
+        const int j = perm[s];
+        int b1[kMaxWidth], b2[kMaxWidth], b3[kMaxWidth];
+        const int n1 = window_bins(m0[(size_t)j * 3 + 0], 0, b1);
+        const int n2 = window_bins(m0[(size_t)j * 3 + 1], 1, b2);
+        const int n3 = window_bins(m0[(size_t)j * 3 + 2], 2, b3);
+        for (int x = 0; x < n1; ++x)
+            for (int y = 0; y < n2; ++y)
+                for (int z = 0; z < n3; ++z)
+                    icnt[((long long)b1[x] * p->nb[1] + b2[y]) * p->nb[2] + b3[z] + 1]++;
+    }
+    for (long long b = 0; b < nbins; ++b) icnt[b + 1] += icnt[b];
+    const long long ninc = icnt[nbins];
+    if (ninc >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
+    p->ninc = ninc;
+    std::vector<int> inc((size_t)std::max(ninc, 1LL));
+    {
+        std::vector<long long> cur(icnt.begin(), icnt.end() - 1);
+        for (long long s = 0; s < J; ++s) {
+            const int j = perm[s];
+            int b1[kMaxWidth], b2[kMaxWidth], b3[kMaxWidth];
+            const int n1 = window_bins(m0[(size_t)j * 3 + 0], 0, b1);
+            const int n2 = window_bins(m0[(size_t)j * 3 + 1], 1, b2);
+            const int n3 = window_bins(m0[(size_t)j * 3 + 2], 2, b3);
+            for (int x = 0; x < n1; ++x)
+                for (int y = 0; y < n2; ++y)
+                    for (int z = 0; z < n3; ++z) {
+                        const long long bin = ((long long)b1[x] * p->nb[1] + b2[y]) * p->nb[2] + b3[z];
+                        inc[cur[bin]++] = (int)s;
+                    }
+        }
+    }
+    // subproblems: every bin (empty ones too, they write zeros), chunks of at most kChunk
+    const long long kChunk = 1024;
+    std::vector<SubProb> subs;
+    long long slots = 0;
+    for (long long b = 0; b < nbins; ++b) {
+        const long long c0 = icnt[b], c1 = icnt[b + 1];
+        const long long n = c1 - c0;
+        const int nch = (int)std::max(1LL, (n + kChunk - 1) / kChunk);
+        for (int ch = 0; ch < nch; ++ch) {
+            SubProb sp;
+            sp.bin = (int)b;
+            sp.start = (int)(c0 + ch * kChunk);
+            sp.count = (int)std::min(kChunk, n - ch * kChunk);
+            if (sp.count < 0) sp.count = 0;
+            sp.chunk = ch;
+            sp.nchunks = nch;
+            sp.slot = nch > 1 ? (int)slots : 0;
+            subs.push_back(sp);
+        }
+        if (nch > 1) slots += nch;
+    }
+    // heaviest subproblems first
+    std::stable_sort(subs.begin(), subs.end(), [](const SubProb& a, const SubProb& b) { return a.count > b.count; });
+    p->nsub = (int)subs.size();
+    p->slots_per_b = slots;
+
+    // ---- device memory ----
+    const size_t Kz = (size_t)K;
+    SDP_TRY(dev_alloc(p, &p->pts, (size_t)J));
+    SDP_TRY(dev_alloc(p, &p->tframe, (size_t)J));
+    SDP_TRY(dev_alloc(p, &p->V, (size_t)d->T * Kz));
+    SDP_TRY(dev_alloc(p, &p->S, (size_t)d->C * nvox));
+    SDP_TRY(dev_alloc(p, &p->dinv, dinv.size()));
+    SDP_TRY(dev_alloc(p, &p->tw, tw.size()));
+    SDP_TRY(dev_alloc(p, &p->inc, inc.size()));
+    SDP_TRY(dev_alloc(p, &p->subs, subs.size()));
+    const size_t P = (size_t)bs[0] * bs[1] * bs[2];
+    SDP_TRY(dev_alloc(p, &p->partials, (size_t)std::max(slots, 1LL) * P * Kz * p->maxB));
+    SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB));
+    SDP_TRY(dev_alloc(p, &p->status, 1));
+    const size_t before = p->total_bytes;
+    const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);
+    const size_t gridB = (size_t)(p->n[0] * p->M[1] * p->M[2]);
+    SDP_TRY(dev_alloc(p, &p->bufA, gridA * Kz * p->maxB));
+    SDP_TRY(dev_alloc(p, &p->bufB, gridB * Kz * p->maxB));
+    p->workspace_bytes = p->total_bytes - before;
+
+    SDP_CUDA(cudaMemcpyAsync(p->pts, pts.data(), pts.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->tframe, tf.data(), tf.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->V, d->V, (size_t)d->T * Kz * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->S, d->coil_maps, (size_t)d->C * nvox * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->dinv, dinv.data(), dinv.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->inc, inc.data(), inc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(SubProb), cudaMemcpyHostToDevice, st));
+    SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * sizeof(int), st));
+    SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    SDP_CUDA(cudaStreamSynchronize(st));
+    size_t o = 0;
+    for (int a = 0; a < 3; ++a) {
+        p->ax[a].tw = p->tw + o;
+        o += (size_t)g.M[a];
+    }
+    return SDP_OK;
+}
+
+// ---- profiling hooks ----
+int prof_begin(sdp_plan_s* p, cudaStream_t st, ProfRec* rec) {
+    if (!p->prof) return SDP_OK;
+    if (p->prof_free.empty()) {
+        ProfRec r;
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return SDP_ERR_CUDA;
+        }
+        p->prof_free.push_back(r);
+    }
+    *rec = p->prof_free.back();
+    p->prof_free.pop_back();
+    SDP_CUDA(cudaEventRecord(rec->a, st));
+    return SDP_OK;
+}
+
+int prof_end(sdp_plan_s* p, cudaStream_t st, ProfRec* rec, int stage) {
+    if (!p->prof) return SDP_OK;
+    rec->stage = stage;
+    SDP_CUDA(cudaEventRecord(rec->b, st));
+    p->prof_used.push_back(*rec);
+    return SDP_OK;
+}
+
+template <typename F>
+int run(sdp_plan_s* p, int stage, cudaStream_t st, F&& f) {
+    ProfRec rec{};
+    SDP_TRY(prof_begin(p, st, &rec));
+    const cudaError_t e = f();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SDP_ERR_CUDA;
+    }
+    return prof_end(p, st, &rec, stage);
+}
+
+const float* dinv_axis(const sdp_plan_s* p, int a) {
+    size_t o = 0;
+    for (int q = 0; q < a; ++q) o += (size_t)p->n[q];
+    return p->dinv + o;
+}
+
+int check_call(const sdp_plan_s* p, const void* in, const int32_t* coil_idx, int B, int k0, int nk,
+               const void* out) {
+    if (!p || !in || !coil_idx || !out) return SDP_ERR_INVALID_ARG;
+    if (B < 1 || B > p->maxB) return SDP_ERR_INVALID_ARG;
+    if (k0 < 0 || nk < 1 || k0 + nk > p->geo.K) return SDP_ERR_INVALID_ARG;
+    return SDP_OK;
+}
+
+int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, int k0, int nk, void* y,
+                 int accumulate, cudaStream_t st) {
+    SDP_TRY(check_call(p, x, coil_idx, B, k0, nk, y));
+    const Geo& g = p->geo;
+    const long long N1 = g.N[0], N2 = g.N[1];
+    const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+    const long long BK = (long long)B * nk;
+    const float2* xs = static_cast<const float2*>(x);
+    SDP_TRY(run(p, ST_FWD_FFT3, st, [&] {
+        return launch_fwd_prologue_fft3(g, p->ax[2], xs, p->S, coil_idx, B, k0, nk, dinv_axis(p, 0),
+                                        dinv_axis(p, 1), dinv_axis(p, 2), p->bufA, p->status, st);
+    }));
+    SDP_TRY(run(p, ST_FWD_FFT2, st, [&] {
+        return launch_fft_strided(p->ax[1], 0, p->bufA, p->bufB, (int)N2, 1, (int)M2, 0, M3, BK * N1, st);
+    }));
+    SDP_TRY(run(p, ST_FWD_FFT1, st, [&] {
+        return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3, BK, st);
+    }));
+    SDP_TRY(run(p, ST_INTERP, st, [&] {
+        return launch_interp(g, p->pts, p->tframe, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y), accumulate,
+                             st);
+    }));
+    return SDP_OK;
+}
+
+int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, int k0, int nk, void* out,
+                 int accumulate, cudaStream_t st) {
+    SDP_TRY(check_call(p, y, coil_idx, B, k0, nk, out));
+    const Geo& g = p->geo;
+    const long long N1 = g.N[0], N2 = g.N[1];
+    const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+    const long long BK = (long long)B * nk;
+    SDP_TRY(run(p, ST_SPREAD, st, [&] {
+        return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->V,
+                             static_cast<const float2*>(y), B, k0, nk, p->bufA, p->partials, p->slots_per_b,
+                             p->counters, p->nbins, st);
+    }));
+    SDP_TRY(run(p, ST_ADJ_FFT1, st, [&] {
+        return launch_fft_strided(p->ax[0], 1, p->bufA, p->bufB, (int)M1, 0, (int)N1, 1, M2 * M3, BK, st);
+    }));
+    SDP_TRY(run(p, ST_ADJ_FFT2, st, [&] {
+        return launch_fft_strided(p->ax[1], 1, p->bufB, p->bufA, (int)M2, 0, (int)N2, 1, M3, BK * N1, st);
+    }));
+    SDP_TRY(run(p, ST_ADJ_FFT3, st, [&] {
+        return launch_adj_fft3_epilogue(g, p->ax[2], p->bufA, p->S, coil_idx, B, k0, nk, dinv_axis(p, 0),
+                                        dinv_axis(p, 1), dinv_axis(p, 2), static_cast<float2*>(out), accumulate,
+                                        p->status, st);
+    }));
+    return SDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* d, void* stream) {
+    if (!out) return SDP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d || !d->traj || !d->V || !d->coil_maps || !d->frame_offsets) return SDP_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (d->n[a] < 2) return SDP_ERR_INVALID_ARG;
+    if (!(d->oversamp >= 1.0 && d->oversamp <= 4.0)) return SDP_ERR_INVALID_ARG;
+    if (d->width < 2 || d->width > kMaxWidth) return SDP_ERR_UNSUPPORTED;
+    if (d->K < 1 || d->K > kMaxK) return SDP_ERR_UNSUPPORTED;
+    if (d->T < 1 || d->C < 1 || d->J < 1 || d->J >= (1LL << 31)) return SDP_ERR_INVALID_ARG;
+    if (d->max_batch < 1 || d->max_batch > kMaxBatch) return SDP_ERR_INVALID_ARG;
+    if (d->frame_offsets[0] != 0 || d->frame_offsets[d->T] != d->J) return SDP_ERR_INVALID_ARG;
+    for (int t = 0; t < d->T; ++t)
+        if (d->frame_offsets[t + 1] < d->frame_offsets[t]) return SDP_ERR_INVALID_ARG;
+    sdp_plan_s* p = new (std::nothrow) sdp_plan_s();
+    if (!p) return SDP_ERR_OOM;
+    if (cudaGetDevice(&p->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return SDP_ERR_CUDA;
+    }
+    const int rc = build_plan(p, d, static_cast<cudaStream_t>(stream));
+    if (rc != SDP_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return SDP_OK;
+}
+
+void sdp_plan_destroy(sdp_plan_t p) { free_plan(p); }
+
+int sdp_forward(sdp_plan_t p, const void* x, const int32_t* coil_idx, int32_t B, void* y, void* stream) {
+    if (!p) return SDP_ERR_INVALID_ARG;
+    return forward_impl(p, x, coil_idx, B, 0, p->geo.K, y, 0, static_cast<cudaStream_t>(stream));
+}
+
+int sdp_adjoint(sdp_plan_t p, const void* y, const int32_t* coil_idx, int32_t B, void* out, int32_t accumulate,
+                void* stream) {
+    if (!p) return SDP_ERR_INVALID_ARG;
+    return adjoint_impl(p, y, coil_idx, B, 0, p->geo.K, out, accumulate ? 1 : 0, static_cast<cudaStream_t>(stream));
+}
+
+int sdp_forward_channels(sdp_plan_t p, const void* x, const int32_t* coil_idx, int32_t B, int32_t k0, int32_t nk,
+                         void* y, int32_t accumulate, void* stream) {
+    return forward_impl(p, x, coil_idx, B, k0, nk, y, accumulate ? 1 : 0, static_cast<cudaStream_t>(stream));
+}
+
+int sdp_adjoint_channels(sdp_plan_t p, const void* y, const int32_t* coil_idx, int32_t B, int32_t k0, int32_t nk,
+                         void* out, int32_t accumulate, void* stream) {
+    return adjoint_impl(p, y, coil_idx, B, k0, nk, out, accumulate ? 1 : 0, static_cast<cudaStream_t>(stream));
+}
+
+int sdp_status(sdp_plan_t p, void* stream) {
+    if (!p) return SDP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return SDP_ERR_CUDA;
+    }
+    int v = 0;
+    if (cudaMemcpy(&v, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SDP_ERR_CUDA;
+    }
+    return v;
+}
+
+int sdp_plan_info(sdp_plan_t p, int64_t* out, int32_t cap) {
+    if (!p || !out || cap < 0) return SDP_ERR_INVALID_ARG;
+    const int64_t v[16] = {p->M[0],        p->M[1],     p->M[2],   p->geo.J,
+                           p->geo.K,       p->maxB,     p->bs[0],  p->bs[1],
+                           p->bs[2],       p->nbins,    p->nsub,   p->ninc,
+                           (int64_t)p->workspace_bytes, (int64_t)p->total_bytes, p->geo.W, p->geo.C};
+    for (int i = 0; i < cap && i < 16; ++i) out[i] = v[i];
+    return SDP_OK;
+}
+
+double sdp_plan_beta(sdp_plan_t p) { return p ? p->beta : -1.0; }
+
+size_t sdp_workspace_bytes(sdp_plan_t p) { return p ? p->workspace_bytes : 0; }
+
+int64_t sdp_launch_count(void) { return g_launches.load(); }
+
+int sdp_profile_enable(sdp_plan_t p, int32_t enable) {
+    if (!p) return SDP_ERR_INVALID_ARG;
+    p->prof = enable != 0;
+    return SDP_OK;
+}
+
+int sdp_profile_read(sdp_plan_t p, double* ms, int64_t* launches, int32_t cap) {
+    if (!p) return -SDP_ERR_INVALID_ARG;
+    for (auto& r : p->prof_used) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return -SDP_ERR_CUDA;
+        }
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return -SDP_ERR_CUDA;
+        }
+        p->prof_ms[r.stage] += t;
+        p->prof_n[r.stage] += 1;
+        p->prof_free.push_back(r);
+    }
+    p->prof_used.clear();
+    const int n = cap < kNumStages ? cap : kNumStages;
+    for (int s = 0; s < n; ++s) {
+        if (ms) ms[s] = p->prof_ms[s];
+        if (launches) launches[s] = p->prof_n[s];
+        p->prof_ms[s] = 0;
+        p->prof_n[s] = 0;
+    }
+    return n;
+}
+
+const char* sdp_strerror(int s) {
+    switch (s) {
+        case SDP_OK: return "ok";
+        case SDP_ERR_INVALID_ARG: return "invalid argument";
+        case SDP_ERR_OOM: return "device out of memory";
+        case SDP_ERR_CUDA: return "CUDA runtime error";
+        case SDP_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SDP_ERR_BOUNDS: return "device-side index out of range (coil index)";
+        case SDP_ERR_UNSUPPORTED: return "unsupported parameters";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

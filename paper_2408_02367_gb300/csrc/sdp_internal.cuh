@@ -1,0 +1,90 @@
+// Internal definitions shared by the kernels and the C ABI of the subspace
+// multicoil NUFFT operator.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/stodip_op.h"
+
+namespace sdp {
+
+constexpr int kMaxRadixStages = 12;
+constexpr int kMaxWidth = 8;
+constexpr int kMaxK = 16;
+constexpr int kMaxBatch = 64;
+constexpr int kNumStages = 8;   // profiling stages, see stodip_op.h
+
+enum Stage {
+    ST_FWD_FFT3 = 0,
+    ST_FWD_FFT2 = 1,
+    ST_FWD_FFT1 = 2,
+    ST_INTERP = 3,
+    ST_SPREAD = 4,
+    ST_ADJ_FFT1 = 5,
+    ST_ADJ_FFT2 = 6,
+    ST_ADJ_FFT3 = 7,
+};
+
+// One axis of the 3D FFT: length L = prod(radix[0..nst)), twiddles
+// tw[m] = exp(-2 pi i m / L) in float32 (computed in float64 on the host).
+struct FftAxis {
+    int L;
+    int nst;
+    int radix[kMaxRadixStages];
+    const float2* tw;
+};
+
+// A spread subproblem: one chunk of the incidence list of one output bin.
+struct SubProb {
+    int bin;       // flattened bin index
+    int start;     // first incidence
+    int count;     // incidences in this chunk
+    int chunk;     // chunk number within the bin
+    int nchunks;   // chunks of this bin (1 = write the bin directly)
+    int slot;      // partial-tile slot of chunk 0 of this bin (multi-chunk bins)
+};
+
+// Shared view of a plan passed to the kernel launchers.
+struct Geo {
+    int N[3];
+    int M[3];
+    int W;
+    int K;
+    int T;
+    int C;
+    int J;
+    float beta;
+    float inv_i0_beta;
+    float halfW;
+};
+
+struct Launch;   // profiling hook, defined in api.cu
+
+// Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
+cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
+                                     const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                     const float* dinv2, const float* dinv3, float2* out, int* status,
+                                     cudaStream_t st);
+cudaError_t launch_fft_strided(const FftAxis& ax, int inverse, const float2* in, float2* out, int n_in,
+                               int in_centred, int n_out, int out_centred, long long inner, long long outer,
+                               cudaStream_t st);
+cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const float2* in, const float2* S,
+                                     const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                     const float* dinv2, const float* dinv3, float2* out, int accumulate,
+                                     int* status, cudaStream_t st);
+cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, const float2* V,
+                          const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
+                          cudaStream_t st);
+cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
+                          const int* inc, const float4* pts, const int* tframe, const float2* V,
+                          const float2* y, int B, int k0, int nk, float2* grids, float2* partials,
+                          long long slots_per_b, int* counters, int nbins, cudaStream_t st);
+
+// Host helpers.
+bool fft_factor(int L, FftAxis* ax);
+std::vector<float2> fft_twiddles(int L);
+
+}  // namespace sdp

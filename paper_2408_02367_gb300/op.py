@@ -1,0 +1,303 @@
+"""Python binding of libstodip_op.so: argument marshalling only.
+
+Every step of the operator runs in the library's CUDA kernels; this module
+checks tensor shapes/dtypes/devices, passes raw device pointers and the current
+CUDA stream through ctypes, and wraps the forward/adjoint pair as a
+torch.autograd.Function whose backward is the library's adjoint (StoDIP
+Algorithm 1: loss.backward() through A_c).  Function names mirror the C ABI of
+include/stodip_op.h.
+
+If the compiled library is missing this module raises on first use: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstodip_op.so")
+
+SDP_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
+                5: "bounds", 6: "unsupported"}
+STAGES = ["fwd_prologue_fft3", "fwd_fft2", "fwd_fft1", "interp", "spread", "adj_ifft1", "adj_ifft2",
+          "adj_ifft3_epilogue"]
+
+
+class SdpError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: status {code} ({_lib_strerror(code)})")
+        self.code = code
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64 * 3),
+        ("oversamp", ctypes.c_double),
+        ("width", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("C", ctypes.c_int32),
+        ("J", ctypes.c_int64),
+        ("max_batch", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("frame_offsets", ctypes.POINTER(ctypes.c_int64)),
+        ("traj", ctypes.c_void_p),
+        ("V", ctypes.c_void_p),
+        ("coil_maps", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+
+EXPORTS = {
+    "sdp_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc), ctypes.c_void_p]),
+    "sdp_plan_destroy": (None, [ctypes.c_void_p]),
+    "sdp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "sdp_forward_channels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_void_p]),
+    "sdp_adjoint_channels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_void_p]),
+    "sdp_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    "sdp_plan_beta": (ctypes.c_double, [ctypes.c_void_p]),
+    "sdp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "sdp_launch_count": (ctypes.c_int64, []),
+    "sdp_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "sdp_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    "sdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Load libstodip_op.so (built by paper_2408_02367_gb300.build) and declare its exports."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                               f"g.build()\"` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _lib_strerror(code):
+    try:
+        return lib().sdp_strerror(int(code)).decode()
+    except Exception:
+        return STATUS_NAMES.get(code, "unknown")
+
+
+def _check(code, what):
+    if code != SDP_OK:
+        raise SdpError(code, what)
+
+
+def _stream_ptr(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require(t, name, dtype, device, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class SubspaceNufft:
+    """Plan of the per-coil subspace NUFFT operator A_c and its adjoint on one GPU.
+
+    traj      float32 [J][3] radians (device), frame_offsets int64 [T+1] (host/CPU),
+    V         complex64 [T][K] (device), coil_maps complex64 [C][N1][N2][N3] (device).
+    """
+
+    def __init__(self, traj, frame_offsets, n, width, oversamp, V, coil_maps, max_batch=1):
+        if not torch.cuda.is_available():
+            raise RuntimeError("SubspaceNufft needs a CUDA device (no CPU fallback)")
+        self.device = traj.device
+        if self.device.type != "cuda":
+            raise ValueError("traj must be a CUDA tensor")
+        L = lib()
+        self.n = tuple(int(v) for v in n)
+        T, K = V.shape
+        C = coil_maps.shape[0]
+        J = traj.shape[0]
+        _require(traj, "traj", torch.float32, self.device, (J, 3))
+        _require(V, "V", torch.complex64, self.device, (T, K))
+        _require(coil_maps, "coil_maps", torch.complex64, self.device, (C,) + self.n)
+        off = np.ascontiguousarray(np.asarray(frame_offsets, dtype=np.int64))
+        if off.shape != (T + 1,):
+            raise ValueError("frame_offsets must have T+1 entries")
+        self._off = off
+        d = PlanDesc()
+        d.n = (ctypes.c_int64 * 3)(*self.n)
+        d.oversamp = float(oversamp)
+        d.width = int(width)
+        d.K, d.T, d.C, d.J = int(K), int(T), int(C), int(J)
+        d.max_batch = int(max_batch)
+        d.flags = 0
+        d.frame_offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.traj = traj.data_ptr()
+        d.V = V.data_ptr()
+        d.coil_maps = coil_maps.data_ptr()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.sdp_plan_create(ctypes.byref(h), ctypes.byref(d), _stream_ptr(self.device)), "sdp_plan_create")
+        self._h = h
+        self.K, self.T, self.C, self.J = int(K), int(T), int(C), int(J)
+        self.max_batch = int(max_batch)
+        self.width = int(width)
+        self.oversamp = float(oversamp)
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sdp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- facts --
+    def info(self):
+        arr = (ctypes.c_int64 * 16)()
+        _check(lib().sdp_plan_info(self._h, arr, 16), "sdp_plan_info")
+        keys = ["M1", "M2", "M3", "J", "K", "max_batch", "bs1", "bs2", "bs3", "nbins", "nsub", "ninc",
+                "workspace_bytes", "total_bytes", "W", "C"]
+        return dict(zip(keys, [int(v) for v in arr]))
+
+    @property
+    def grid(self):
+        i = self.info()
+        return (i["M1"], i["M2"], i["M3"])
+
+    @property
+    def beta(self):
+        return float(lib().sdp_plan_beta(self._h))
+
+    def status(self):
+        """Synchronise the current stream and return (and clear) the device status word."""
+        return int(lib().sdp_status(self._h, _stream_ptr(self.device)))
+
+    # -- argument checks --
+    def _coils(self, coil_idx):
+        _require(coil_idx, "coil_idx", torch.int32, self.device)
+        if coil_idx.dim() != 1 or not (1 <= coil_idx.numel() <= self.max_batch):
+            raise ValueError(f"coil_idx must be 1-D with 1..{self.max_batch} entries")
+        return coil_idx.numel()
+
+    # -- operator --
+    def forward(self, x, coil_idx, out=None, k0=0, nk=None, accumulate=False):
+        """y[b] = A_{coil_idx[b]}(x) (channels k0..k0+nk of x when given), y [B][J] complex64."""
+        B = self._coils(coil_idx)
+        _require(x, "x", torch.complex64, self.device, (self.K,) + self.n)
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate needs out")
+            out = torch.empty((B, self.J), dtype=torch.complex64, device=self.device)
+        _require(out, "y", torch.complex64, self.device, (B, self.J))
+        st = _stream_ptr(self.device)
+        if nk is None and k0 == 0 and not accumulate:
+            rc = lib().sdp_forward(self._h, _dev_ptr(x), _dev_ptr(coil_idx), B, _dev_ptr(out), st)
+        else:
+            nk = self.K - k0 if nk is None else nk
+            rc = lib().sdp_forward_channels(self._h, _dev_ptr(x), _dev_ptr(coil_idx), B, int(k0), int(nk),
+                                            _dev_ptr(out), int(bool(accumulate)), st)
+        _check(rc, "sdp_forward")
+        return out
+
+    def adjoint(self, y, coil_idx, out=None, accumulate=False, k0=0, nk=None):
+        """out_k (+)= sum_b A_{coil_idx[b]}^H y[b], out [K][N1][N2][N3] complex64."""
+        B = self._coils(coil_idx)
+        _require(y, "y", torch.complex64, self.device, (B, self.J))
+        if out is None:
+            out = (torch.zeros if (accumulate or nk is not None) else torch.empty)(
+                (self.K,) + self.n, dtype=torch.complex64, device=self.device)
+        _require(out, "out", torch.complex64, self.device, (self.K,) + self.n)
+        st = _stream_ptr(self.device)
+        if nk is None and k0 == 0:
+            rc = lib().sdp_adjoint(self._h, _dev_ptr(y), _dev_ptr(coil_idx), B, _dev_ptr(out),
+                                   int(bool(accumulate)), st)
+        else:
+            nk = self.K - k0 if nk is None else nk
+            rc = lib().sdp_adjoint_channels(self._h, _dev_ptr(y), _dev_ptr(coil_idx), B, int(k0), int(nk),
+                                            _dev_ptr(out), int(bool(accumulate)), st)
+        _check(rc, "sdp_adjoint")
+        return out
+
+    # -- profiling --
+    def profile(self, enable=True):
+        _check(lib().sdp_profile_enable(self._h, int(bool(enable))), "sdp_profile_enable")
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 8)()
+        nl = (ctypes.c_int64 * 8)()
+        n = lib().sdp_profile_read(self._h, ms, nl, 8)
+        if n < 0:
+            raise SdpError(-n, "sdp_profile_read")
+        return {STAGES[i]: (float(ms[i]), int(nl[i])) for i in range(n)}
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().sdp_launch_count())
+
+
+class _ApplyA(torch.autograd.Function):
+    """y = A_B(x) with backward grad_x = A_B^H grad_y (PyTorch's conjugate-Wirtinger
+    convention makes the vector-Jacobian product of a linear complex map its adjoint)."""
+
+    @staticmethod
+    def forward(ctx, x, coil_idx, op):
+        ctx.op = op
+        ctx.save_for_backward(coil_idx)
+        return op.forward(x.contiguous(), coil_idx)
+
+    @staticmethod
+    def backward(ctx, gy):
+        (coil_idx,) = ctx.saved_tensors
+        gx = ctx.op.adjoint(gy.contiguous(), coil_idx) if ctx.needs_input_grad[0] else None
+        return gx, None, None
+
+
+def apply_A(op: SubspaceNufft, x, coil_idx):
+    """Differentiable A_B(x) for a coil minibatch coil_idx (Algorithm 1, lines 4 and 7)."""
+    return _ApplyA.apply(x, coil_idx, op)
+
+
+def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda"):
+    """Plan from numpy inputs (omega float32 [J][3], frame int [J] non-decreasing)."""
+    T = V.shape[0]
+    off = np.searchsorted(np.asarray(frame), np.arange(T + 1), side="left").astype(np.int64)
+    off[-1] = len(frame)
+    dev = torch.device(device)
+    return SubspaceNufft(torch.from_numpy(np.ascontiguousarray(omega, np.float32)).to(dev), off, n, width,
+                         oversamp, torch.from_numpy(np.ascontiguousarray(V, np.complex64)).to(dev),
+                         torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev), max_batch=max_batch)
