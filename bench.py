@@ -1,0 +1,502 @@
+#!/usr/bin/env python
+"""Benchmark of one StoDIP data-consistency step on the subspace multicoil NUFFT operator.
+
+One step = Algorithm 1, lines 4, 5 and 7 (DCF = 1, no TV term) on a coil
+minibatch drawn uniformly without replacement:
+    yhat = A_B(x_hat);  L = sum_b ||yhat_b - y_{c_b}||^2;  L.backward()
+i.e. the forward operator, the residual/loss and the autograd adjoint
+A_B^H(2r), all in libstodip_op.so kernels, with x_hat a fixed complex TSMI
+that requires grad (the generator G_theta is not part of the operator).
+
+Workload (default): 128^3 image, K=5 subspace channels, C=8 coils, T=480
+frames of one 1024-sample golden-angle 3D spiral arm (J=491,520 samples per
+coil), Kaiser-Bessel W=4 on a 1.25x oversampled grid (160^3), B=2 coils per
+step.  Synthetic seeded inputs (phantom, coil maps, trajectory, V).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2408_02367_gb300 import synth  # noqa: E402
+
+METRIC = "DIP step ms (A_c fwd + autograd A_c^H) and NU samples/s at 1e-4 rel err vs plain"
+UNIT = "NU samples/s"
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 256 * 1024 * 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_desc(w, B):
+    return (f"{w.name}: {w.n[0]}x{w.n[1]}x{w.n[2]} image, K={w.K} subspace channels, C={w.C} coils, "
+            f"T={w.T} frames x {w.arms} golden-angle 3D spiral arm(s) x {w.arm_len} samples "
+            f"(J={w.J} per coil), Kaiser-Bessel W={w.width}, sigma={w.oversamp}, coil minibatch B={B}")
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (replicas: each rank runs its own coil minibatches)
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Coil-draw seed of one replica: independent minibatch streams per rank."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest per-rank value (the slowest replica sets the job time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id=None, interval_ms=100):
+        self.gpu_id = gpu_id
+        self.interval_ms = interval_ms
+        self.lines = []
+        self.proc = None
+        self.err = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", str(self.interval_ms)]
+        if self.gpu_id:
+            cmd.insert(1, f"--id={self.gpu_id}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:   # nvidia-smi missing
+            self.err = str(e)
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "error": self.err}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, pw, reasons = [], [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel (the HBM roofline model)
+# ----------------------------------------------------------------------------
+
+def stage_bytes(w, B, M, ninc):
+    """Bytes each kernel must move per launch (read + write, complex64 = 8 B).
+
+    The oversampled grid of every (coil, channel) is written once and read once
+    per pass; x, S, y and the sample tables are read once."""
+    N1, N2, N3 = w.n
+    M1, M2, M3 = M
+    K, J = w.K, w.J
+    nvox = N1 * N2 * N3
+    G = M1 * M2 * M3
+    c = 8
+    return {
+        "fwd_prologue_fft3": c * (K * nvox + B * nvox + B * K * N1 * N2 * M3),
+        "fwd_fft2": c * B * K * (N1 * N2 * M3 + N1 * M2 * M3),
+        "fwd_fft1": c * B * K * (N1 * M2 * M3 + G),
+        "interp": c * B * K * G + 20 * J + c * B * J,
+        "residual_loss": 3 * c * B * J,
+        "spread": c * B * J + 20 * J + 4 * ninc + c * B * K * G,
+        "adj_ifft1": c * B * K * (G + N1 * M2 * M3),
+        "adj_ifft2": c * B * K * (N1 * M2 * M3 + N1 * N2 * M3),
+        "adj_ifft3_epilogue": c * (B * K * N1 * N2 * M3 + B * nvox + K * nvox),
+    }
+
+
+def path_model_bytes(w, B, M):
+    """Whole-step model: 8 K Nvox + B (8 Nvox + 16 K G + 8 J) + 12 J per direction."""
+    nvox = int(np.prod(w.n))
+    G = int(np.prod(M))
+    one = 8 * w.K * nvox + B * (8 * nvox + 16 * w.K * G + 8 * w.J) + 12 * w.J
+    return 2 * one
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample_step(w, problem, geo, coil, k, frames, O):
+    """One coil, one channel, a contiguous block of frames: the six oracle steps timed.
+
+    Returns (t_grid_steps, t_sample_steps, n_samples): the deapod/FFT steps cost
+    the same for any sample count, the interpolation/spread steps scale with it."""
+    x, S, V, omega, frame = problem
+    sel = (frame >= frames[0]) & (frame < frames[1])
+    om = omega[sel]
+    fr = frame[sel]
+    g32 = O.grid_coords(om, geo.M)
+    t0 = time.perf_counter()
+    U = O.fwd_fft(O.fwd_prologue(geo, x[k], S[coil]))
+    t1 = time.perf_counter()
+    yk = O.fwd_interp(geo, U[None], V[:, k:k + 1], g32, fr)
+    t2 = time.perf_counter()
+    H = O.adj_spread(geo, yk, V[:, k:k + 1], g32, fr)
+    t3 = time.perf_counter()
+    O.adj_epilogue(geo, O.adj_ifft(H[0]), S[coil])
+    t4 = time.perf_counter()
+    return (t1 - t0) + (t4 - t3), (t2 - t1) + (t3 - t2), int(sel.sum())
+
+
+def oracle_step_seconds(w, B, tg, ts, ns):
+    """Oracle seconds for a whole step: B coils x K channels, all J samples."""
+    return B * w.K * (tg + ts * (w.J / ns))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import nufft as O
+    w = synth.WORKLOADS[args.workload]
+    B = w.batch
+    problem = synth.make_problem(w)
+    geo = O.Geometry(w.n, w.width, w.oversamp)
+    frames = (0, max(1, w.T // 16))
+    rng = np.random.default_rng(rank_seed(synth.SEED_COILS_DRAW, rank))
+    times = []
+    for i in range(args.warmup + args.steps):
+        coil = int(rng.integers(0, w.C))
+        k = i % w.K
+        tg, ts, ns = oracle_sample_step(w, problem, geo, coil, k, frames, O)
+        if i >= args.warmup:
+            times.append(oracle_step_seconds(w, B, tg, ts, ns))
+    t = float(np.mean(times))
+    value = B * w.J / t
+    sample = (f"per step: FP64 oracle (numpy, 1 thread) forward+adjoint of 1 coil x 1 channel on the full "
+              f"{geo.M[0]}x{geo.M[1]}x{geo.M[2]} grid with frames {frames[0]}..{frames[1] - 1} "
+              f"({ns} samples); time scaled to B*K coil-channels and J samples per coil")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(w, B), "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cpus": os.cpu_count()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(w, B, budget_s=20.0):
+    from oracle import nufft as O
+    problem = synth.make_problem(w)
+    geo = O.Geometry(w.n, w.width, w.oversamp)
+    frames = (0, max(1, w.T // 4))
+    t_start = time.perf_counter()
+    ests = []
+    k = 0
+    while not ests or (time.perf_counter() - t_start < budget_s and len(ests) < 4):
+        tg, ts, ns = oracle_sample_step(w, problem, geo, 1, k % w.K, frames, O)
+        ests.append(oracle_step_seconds(w, B, tg, ts, ns))
+        k += 1
+    t = float(np.median(ests))
+    return {"value": B * w.J / t, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cpus": os.cpu_count(),
+            "sample": (f"{len(ests)} runs of the FP64 oracle (numpy, 1 thread) forward+adjoint for 1 coil x 1 "
+                       f"channel on the full {geo.M[0]}x{geo.M[1]}x{geo.M[2]} grid with frames "
+                       f"{frames[0]}..{frames[1] - 1} ({ns} samples), scaled to B*K coil-channels and J "
+                       f"samples per coil; median"),
+            "seconds_per_step": t}
+
+
+# ----------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2408_02367_gb300 import op
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload]
+    B = args.batch or w.batch
+
+    x_true, S, V, omega, frame = synth.make_problem(w)
+    x_hat = synth.ellipsoid_phantom(w.n, w.K, seed=1)
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=max(B, 1), device=dev)
+    info = A.info()
+    M = (info["M1"], info["M2"], info["M3"])
+
+    # measured k-space of every coil: A_c(x_true) + complex noise at 30 dB SNR
+    xt = torch.from_numpy(x_true).to(dev)
+    y_meas = torch.empty((w.C, w.J), dtype=torch.complex64, device=dev)
+    for c in range(w.C):
+        A.forward(xt, torch.tensor([c], dtype=torch.int32, device=dev), out=y_meas[c:c + 1])
+    sig = float(torch.linalg.norm(y_meas).item()) ** 2 / (y_meas.numel() * 1e3)
+    y_meas += torch.from_numpy(synth.complex_noise((w.C, w.J), math.sqrt(sig))).to(dev)
+    del xt
+
+    nsteps = args.warmup + args.steps
+    draws = synth.coil_minibatches(w.C, B, nsteps, seed=rank_seed(synth.SEED_COILS_DRAW, rank))
+    coil_dev = torch.from_numpy(np.stack(draws)).to(dev)        # [steps][B], resident
+    x = torch.from_numpy(x_hat).to(dev).requires_grad_(True)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def dip_step(ci):
+        x.grad = None
+        loss = op.dc_loss(A, x, ci, y_meas)
+        loss.backward()
+        return loss
+
+    # ---- correctness gate vs the plain form (one coil, one channel per launch) ----
+    ci0 = coil_dev[0].contiguous()
+    loss_b = dip_step(ci0)
+    g_b = x.grad.clone()
+    y_b = A.forward(x.detach(), ci0)
+    y_p = torch.zeros_like(y_b)
+    g_p = torch.zeros_like(g_b)
+
+    def plain_step(ci):
+        y_p.zero_()
+        for b in range(B):
+            for k in range(w.K):
+                A.forward(x.detach(), ci[b:b + 1], out=y_p[b:b + 1], k0=k, nk=1, accumulate=True)
+        r2, lossp = A.residual_loss(y_p, y_meas, ci)
+        g_p.zero_()
+        for b in range(B):
+            for k in range(w.K):
+                A.adjoint(r2[b:b + 1].contiguous(), ci[b:b + 1], out=g_p, accumulate=True, k0=k, nk=1)
+        return lossp
+
+    loss_p = plain_step(ci0)
+    torch.cuda.synchronize()
+    rel_y = float(torch.linalg.norm(y_p - y_b) / torch.linalg.norm(y_b))
+    rel_g = float(torch.linalg.norm(g_p - g_b) / torch.linalg.norm(g_b))
+    rel_l = abs(float(loss_p) - float(loss_b)) / abs(float(loss_b))
+    assert A.status() == 0
+    rel_vs_plain = max(rel_y, rel_g, rel_l)
+    if rel_vs_plain > 1e-4:
+        raise SystemExit(f"batched path differs from the plain form: {rel_vs_plain:.3e}")
+
+    # ---- eager timed region ----
+    def timed(fn, steps, start_index, profile):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if profile:
+            A.profile(True)
+            A.profile_read()
+        n0 = op.launch_count()
+        for i in range(steps):
+            flush.fill_(float(i))                # L2 flush, outside the events
+            evs[i][0].record()
+            fn(coil_dev[start_index + i])
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        launches = op.launch_count() - n0
+        prof = A.profile_read() if profile else None
+        if profile:
+            A.profile(False)
+        return sum(a.elapsed_time(b) for a, b in evs), launches, prof
+
+    for i in range(args.warmup):
+        flush.fill_(0.0)
+        dip_step(coil_dev[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gpu_id = None
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        gpu_id = "GPU-" + str(u)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id).start()
+    total_ms, launches, prof = timed(dip_step, args.steps, args.warmup, True)
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = max_over_ranks(total_ms, dist, dev)
+    ms = total_ms / args.steps
+    value = ws * B * w.J / (ms * 1e-3)
+
+    # ---- plain form, same draws, fewer steps ----
+    n_plain = min(args.steps, 20)
+    plain_ms, plain_launches, _ = timed(plain_step, n_plain, args.warmup, False)
+    plain_ms /= n_plain
+
+    # ---- end to end through the public API with host buffers ----
+    xh = torch.from_numpy(x_hat).pin_memory()
+    yh = torch.empty((B, w.J), dtype=torch.complex64).pin_memory()
+    ch = torch.empty((B,), dtype=torch.int32).pin_memory()
+    gh = torch.empty((w.K,) + tuple(w.n), dtype=torch.complex64).pin_memory()
+    lh = torch.empty((), dtype=torch.float32).pin_memory()
+    ymh = y_meas.cpu()
+    meas_rows = torch.arange(B, dtype=torch.int32, device=dev)
+    x_e = torch.empty_like(x.detach())
+    y_e = torch.empty((B, w.J), dtype=torch.complex64, device=dev)
+    c_e = torch.empty((B,), dtype=torch.int32, device=dev)
+    n_e2e = min(args.steps, 50)
+    e2e_steps = [(draws[args.warmup + i], ymh[torch.from_numpy(draws[args.warmup + i].astype(np.int64))])
+                 for i in range(n_e2e)]
+
+    def e2e_step(i):
+        cdraw, ysel = e2e_steps[i]
+        ch.copy_(torch.from_numpy(cdraw))
+        yh.copy_(ysel)
+        c_e.copy_(ch, non_blocking=True)
+        y_e.copy_(yh, non_blocking=True)
+        x_e.copy_(xh, non_blocking=True)
+        x_e.requires_grad_(True)
+        x_e.grad = None
+        loss = op.dc_loss(A, x_e, c_e, y_e, meas_rows)
+        loss.backward()
+        gh.copy_(x_e.grad, non_blocking=True)
+        lh.copy_(loss.detach(), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        x_e.requires_grad_(False)
+
+    e2e_step(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        e2e_step(i)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    h2d = xh.numel() * 8 + yh.numel() * 8 + ch.numel() * 4
+    d2h = gh.numel() * 8 + 4
+
+    # ---- roofline of the dominant kernel ----
+    hbm, peak_kind = peaks()
+    sb = stage_bytes(w, B, M, info["ninc"])
+    stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+    dom = max(stages, key=lambda k: stages[k]["ms_total"])
+    avg_ms = stages[dom]["ms_total"] / stages[dom]["launches"]
+    achieved = sb[dom] / (avg_ms * 1e-3) / 1e9
+    step_share = {k: round(v["ms_total"] / sum(s["ms_total"] for s in stages.values()), 4) for k, v in stages.items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, B, budget_s=args.cpu_budget)
+
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    model = path_model_bytes(w, B, M)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(w, B), "grid": list(M), "l2": "flushed between steps "
+                   f"({FLUSH_BYTES >> 20} MiB write outside the timed events)", "parallelism":
+                   "replicas" if ws > 1 else "single GPU", "coil_draws": "uniform without replacement, "
+                   "pre-drawn and resident on the device"},
+        "dip_step_ms": ms,
+        "plain_form": {"ms_per_step": plain_ms, "launches_per_step": plain_launches / n_plain,
+                       "rel_err_vs_plain": rel_vs_plain, "speedup": plain_ms / ms},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms},
+        "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
+        "stage_share": step_share,
+        "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (ms * 1e-3)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * B * w.J / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3, "steps": n_e2e},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="vol128_w4", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -145,6 +145,30 @@ int sdp_adjoint_channels(sdp_plan_t plan, const void* y, const int32_t* coil_idx
                          int32_t k0, int32_t nk, void* out, int32_t accumulate, void* stream);
 
 /*
+ * Adjoint with the input scaled by a DEVICE float32 scalar:
+ *   out_k = (accumulate ? out_k : 0) + (*scale) * sum_b A_{coil_idx[b]}^H (y[b]).
+ * The scale is read by the kernel, so an autograd backward can pass the
+ * incoming gradient of a scalar loss without a host synchronisation.
+ */
+int sdp_adjoint_scaled(sdp_plan_t plan, const void* y, const int32_t* coil_idx, int32_t B, const float* scale,
+                       void* out, int32_t accumulate, void* stream);
+
+/*
+ * Data-consistency residual and loss of Eq. 3 (DCF = 1), Algorithm 1 line 5,
+ * summed over the minibatch:
+ *   r2[b][j] = 2 (yhat[b][j] - y_meas[meas_idx[b]][j])   (dL/dyhat, PyTorch convention)
+ *   *loss    = sum_b sum_j |yhat[b][j] - y_meas[meas_idx[b]][j]|^2
+ *   yhat      DEVICE complex64 [B][J]
+ *   y_meas    DEVICE complex64 [n_meas_rows][J] (e.g. all C coils, or one row per b)
+ *   meas_idx  DEVICE int32 [B], rows of y_meas, each in [0, n_meas_rows)
+ *   r2        DEVICE complex64 [B][J] (overwritten)
+ *   loss      DEVICE float32 scalar (overwritten); accumulated in float64 and
+ *             summed in a fixed order, so it is bitwise repeatable.
+ */
+int sdp_residual_loss(sdp_plan_t plan, const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                      const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream);
+
+/*
  * Synchronise `stream`, return the plan's device status word (SDP_OK or the
  * first device-side error recorded since the last call) and clear it.
  */
@@ -177,7 +201,7 @@ int64_t sdp_launch_count(void);
  * writes up to `cap` stages: ms[s] = summed milliseconds, launches[s] = count.
  * Stages: 0 prologue+FFT axis 3, 1 FFT axis 2, 2 FFT axis 1, 3 interpolation,
  * 4 spread, 5 inverse FFT axis 1, 6 inverse FFT axis 2, 7 inverse FFT axis 3
- * + epilogue.  Reading resets the sums.  Returns the number of stages written
+ * + epilogue, 8 residual and loss.  Reading resets the sums.  Returns the number of stages written
  * or a negative status.  Profiling is off by default and costs two event
  * records per launch when on.
  */

@@ -53,6 +53,8 @@ struct sdp_plan_s {
     float2* partials = nullptr;
     int* counters = nullptr;
     int* status = nullptr;
+    double* loss_partials = nullptr;
+    unsigned int* loss_counter = nullptr;
     float2* bufA = nullptr;
     float2* bufB = nullptr;
     size_t workspace_bytes = 0;
@@ -359,6 +361,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_TRY(dev_alloc(p, &p->partials, (size_t)std::max(slots, 1LL) * P * Kz * p->maxB));
     SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB));
     SDP_TRY(dev_alloc(p, &p->status, 1));
+    SDP_TRY(dev_alloc(p, &p->loss_partials, (size_t)residual_loss_blocks()));
+    SDP_TRY(dev_alloc(p, &p->loss_counter, 1));
     const size_t before = p->total_bytes;
     const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);
     const size_t gridB = (size_t)(p->n[0] * p->M[1] * p->M[2]);
@@ -376,6 +380,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_CUDA(cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(SubProb), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+    SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
     SDP_CUDA(cudaStreamSynchronize(st));
     size_t o = 0;
     for (int a = 0; a < 3; ++a) {
@@ -463,7 +468,7 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
 }
 
 int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, int k0, int nk, void* out,
-                 int accumulate, cudaStream_t st) {
+                 int accumulate, const float* scale, cudaStream_t st) {
     SDP_TRY(check_call(p, y, coil_idx, B, k0, nk, out));
     const Geo& g = p->geo;
     const long long N1 = g.N[0], N2 = g.N[1];
@@ -471,7 +476,7 @@ int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, i
     const long long BK = (long long)B * nk;
     SDP_TRY(run(p, ST_SPREAD, st, [&] {
         return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->V,
-                             static_cast<const float2*>(y), B, k0, nk, p->bufA, p->partials, p->slots_per_b,
+                             static_cast<const float2*>(y), scale, B, k0, nk, p->bufA, p->partials, p->slots_per_b,
                              p->counters, p->nbins, st);
     }));
     SDP_TRY(run(p, ST_ADJ_FFT1, st, [&] {
@@ -532,7 +537,27 @@ int sdp_forward(sdp_plan_t p, const void* x, const int32_t* coil_idx, int32_t B,
 int sdp_adjoint(sdp_plan_t p, const void* y, const int32_t* coil_idx, int32_t B, void* out, int32_t accumulate,
                 void* stream) {
     if (!p) return SDP_ERR_INVALID_ARG;
-    return adjoint_impl(p, y, coil_idx, B, 0, p->geo.K, out, accumulate ? 1 : 0, static_cast<cudaStream_t>(stream));
+    return adjoint_impl(p, y, coil_idx, B, 0, p->geo.K, out, accumulate ? 1 : 0, nullptr,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int sdp_adjoint_scaled(sdp_plan_t p, const void* y, const int32_t* coil_idx, int32_t B, const float* scale,
+                       void* out, int32_t accumulate, void* stream) {
+    if (!p || !scale) return SDP_ERR_INVALID_ARG;
+    return adjoint_impl(p, y, coil_idx, B, 0, p->geo.K, out, accumulate ? 1 : 0, scale,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int sdp_residual_loss(sdp_plan_t p, const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                      const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream) {
+    if (!p || !yhat || !y_meas || !meas_idx || !r2 || !loss) return SDP_ERR_INVALID_ARG;
+    if (B < 1 || B > p->maxB || n_meas_rows < 1) return SDP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return run(p, ST_LOSS, st, [&] {
+        return launch_residual_loss(static_cast<const float2*>(yhat), static_cast<const float2*>(y_meas), meas_idx,
+                                    B, (long long)p->geo.J, n_meas_rows, static_cast<float2*>(r2),
+                                    p->loss_partials, p->loss_counter, loss, p->status, st);
+    });
 }
 
 int sdp_forward_channels(sdp_plan_t p, const void* x, const int32_t* coil_idx, int32_t B, int32_t k0, int32_t nk,
@@ -542,7 +567,7 @@ int sdp_forward_channels(sdp_plan_t p, const void* x, const int32_t* coil_idx, i
 
 int sdp_adjoint_channels(sdp_plan_t p, const void* y, const int32_t* coil_idx, int32_t B, int32_t k0, int32_t nk,
                          void* out, int32_t accumulate, void* stream) {
-    return adjoint_impl(p, y, coil_idx, B, k0, nk, out, accumulate ? 1 : 0, static_cast<cudaStream_t>(stream));
+    return adjoint_impl(p, y, coil_idx, B, k0, nk, out, accumulate ? 1 : 0, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 int sdp_status(sdp_plan_t p, void* stream) {

@@ -15,7 +15,7 @@ constexpr int kMaxRadixStages = 12;
 constexpr int kMaxWidth = 8;
 constexpr int kMaxK = 16;
 constexpr int kMaxBatch = 64;
-constexpr int kNumStages = 8;   // profiling stages, see stodip_op.h
+constexpr int kNumStages = 9;   // profiling stages, see stodip_op.h
 
 enum Stage {
     ST_FWD_FFT3 = 0,
@@ -26,6 +26,7 @@ enum Stage {
     ST_ADJ_FFT1 = 5,
     ST_ADJ_FFT2 = 6,
     ST_ADJ_FFT3 = 7,
+    ST_LOSS = 8,
 };
 
 // One axis of the 3D FFT: length L = prod(radix[0..nst)), twiddles
@@ -80,8 +81,12 @@ cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, co
                           cudaStream_t st);
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
                           const int* inc, const float4* pts, const int* tframe, const float2* V,
-                          const float2* y, int B, int k0, int nk, float2* grids, float2* partials,
-                          long long slots_per_b, int* counters, int nbins, cudaStream_t st);
+                          const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
+                          float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
+int residual_loss_blocks();
+cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
+                                 int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
+                                 int* status, cudaStream_t st);
 
 // Host helpers.
 bool fft_factor(int L, FftAxis* ax);

@@ -38,6 +38,7 @@ struct SpreadArgs {
     const int* tframe;
     const float2* V;
     const float2* y;
+    const float* scale;
     int k0, nk;
     float2* grids;
     float2* partials;
@@ -78,7 +79,12 @@ __global__ void __launch_bounds__(kThreads) spread_kernel(SpreadArgs a) {
         const float4 p = __ldg(a.pts + s);
         const int orig = __float_as_int(p.w);
         const int t = __ldg(a.tframe + s);
-        const float2 r = __ldg(yb + orig);
+        float2 r = __ldg(yb + orig);
+        if (a.scale) {
+            const float sc = __ldg(a.scale);
+            r.x *= sc;
+            r.y *= sc;
+        }
         const int m01 = (int)ceilf(p.x - g.halfW);
         const int m02 = (int)ceilf(p.y - g.halfW);
         const int m03 = (int)ceilf(p.z - g.halfW);
@@ -187,8 +193,8 @@ cudaError_t launch_w(const SpreadArgs& a, int nsub, int B, size_t smem, cudaStre
 
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
                           const int* inc, const float4* pts, const int* tframe, const float2* V,
-                          const float2* y, int B, int k0, int nk, float2* grids, float2* partials,
-                          long long slots_per_b, int* counters, int nbins, cudaStream_t st) {
+                          const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
+                          float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st) {
     SpreadArgs a;
     a.g = g;
     a.bs1 = bs[0];
@@ -203,6 +209,7 @@ cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const 
     a.tframe = tframe;
     a.V = V;
     a.y = y;
+    a.scale = scale;
     a.k0 = k0;
     a.nk = nk;
     a.grids = grids;

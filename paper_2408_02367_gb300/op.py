@@ -25,7 +25,7 @@ SDP_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
                 5: "bounds", 6: "unsupported"}
 STAGES = ["fwd_prologue_fft3", "fwd_fft2", "fwd_fft1", "interp", "spread", "adj_ifft1", "adj_ifft2",
-          "adj_ifft3_epilogue"]
+          "adj_ifft3_epilogue", "residual_loss"]
 
 
 class SdpError(RuntimeError):
@@ -67,6 +67,11 @@ EXPORTS = {
     "sdp_adjoint_channels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_void_p]),
+    "sdp_adjoint_scaled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "sdp_residual_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "sdp_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sdp_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "sdp_plan_beta": (ctypes.c_double, [ctypes.c_void_p]),
@@ -252,14 +257,45 @@ class SubspaceNufft:
         _check(rc, "sdp_adjoint")
         return out
 
+    def adjoint_scaled(self, y, coil_idx, scale, out=None, accumulate=False):
+        """out_k (+)= (*scale) sum_b A^H y[b] with `scale` a 0-dim float32 device tensor."""
+        B = self._coils(coil_idx)
+        _require(y, "y", torch.complex64, self.device, (B, self.J))
+        _require(scale, "scale", torch.float32, self.device, ())
+        if out is None:
+            out = torch.empty((self.K,) + self.n, dtype=torch.complex64, device=self.device)
+        _require(out, "out", torch.complex64, self.device, (self.K,) + self.n)
+        _check(lib().sdp_adjoint_scaled(self._h, _dev_ptr(y), _dev_ptr(coil_idx), B, _dev_ptr(scale),
+                                        _dev_ptr(out), int(bool(accumulate)), _stream_ptr(self.device)),
+               "sdp_adjoint_scaled")
+        return out
+
+    def residual_loss(self, yhat, y_meas, meas_idx, r2=None, loss=None):
+        """r2 = 2 (yhat - y_meas[meas_idx]) and loss = sum |yhat - y_meas[meas_idx]|^2 (device scalar)."""
+        B = self._coils(meas_idx)
+        _require(yhat, "yhat", torch.complex64, self.device, (B, self.J))
+        if y_meas.dim() != 2 or y_meas.shape[1] != self.J:
+            raise ValueError("y_meas must be [rows][J]")
+        _require(y_meas, "y_meas", torch.complex64, self.device)
+        if r2 is None:
+            r2 = torch.empty_like(yhat)
+        if loss is None:
+            loss = torch.empty((), dtype=torch.float32, device=self.device)
+        _require(r2, "r2", torch.complex64, self.device, (B, self.J))
+        _require(loss, "loss", torch.float32, self.device, ())
+        _check(lib().sdp_residual_loss(self._h, _dev_ptr(yhat), _dev_ptr(y_meas), int(y_meas.shape[0]),
+                                       _dev_ptr(meas_idx), B, _dev_ptr(r2), _dev_ptr(loss),
+                                       _stream_ptr(self.device)), "sdp_residual_loss")
+        return r2, loss
+
     # -- profiling --
     def profile(self, enable=True):
         _check(lib().sdp_profile_enable(self._h, int(bool(enable))), "sdp_profile_enable")
 
     def profile_read(self):
-        ms = (ctypes.c_double * 8)()
-        nl = (ctypes.c_int64 * 8)()
-        n = lib().sdp_profile_read(self._h, ms, nl, 8)
+        ms = (ctypes.c_double * len(STAGES))()
+        nl = (ctypes.c_int64 * len(STAGES))()
+        n = lib().sdp_profile_read(self._h, ms, nl, len(STAGES))
         if n < 0:
             raise SdpError(-n, "sdp_profile_read")
         return {STAGES[i]: (float(ms[i]), int(nl[i])) for i in range(n)}
@@ -290,6 +326,37 @@ class _ApplyA(torch.autograd.Function):
 def apply_A(op: SubspaceNufft, x, coil_idx):
     """Differentiable A_B(x) for a coil minibatch coil_idx (Algorithm 1, lines 4 and 7)."""
     return _ApplyA.apply(x, coil_idx, op)
+
+
+class _DataConsistency(torch.autograd.Function):
+    """L = sum_b ||A_{c_b}(x) - y_meas[row_b]||^2 (Eq. 3, DCF = 1) with the whole
+    forward (operator + residual + loss) and backward (scaled adjoint of 2r) in
+    the library's kernels."""
+
+    @staticmethod
+    def forward(ctx, x, coil_idx, meas_idx, y_meas, op):
+        yhat = op.forward(x.contiguous(), coil_idx)
+        r2, loss = op.residual_loss(yhat, y_meas, meas_idx, r2=yhat)   # r2 overwrites yhat in place
+        ctx.op = op
+        ctx.save_for_backward(coil_idx, r2)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gL):
+        coil_idx, r2 = ctx.saved_tensors
+        gx = None
+        if ctx.needs_input_grad[0]:
+            gx = ctx.op.adjoint_scaled(r2, coil_idx, gL.to(torch.float32).contiguous())
+        return gx, None, None, None, None
+
+
+def dc_loss(op: SubspaceNufft, x, coil_idx, y_meas, meas_idx=None):
+    """Differentiable data-consistency loss of a coil minibatch (Algorithm 1, lines 4-5).
+
+    y_meas [rows][J]: measured k-space; row meas_idx[b] is compared with coil
+    coil_idx[b] (default meas_idx = coil_idx, i.e. y_meas holds all C coils).
+    """
+    return _DataConsistency.apply(x, coil_idx, coil_idx if meas_idx is None else meas_idx, y_meas, op)
 
 
 def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda"):
