@@ -169,6 +169,30 @@ int sdp_residual_loss(sdp_plan_t plan, const void* yhat, const void* y_meas, int
                       const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream);
 
 /*
+ * Residual and loss of sdp_residual_loss without a plan and without any device
+ * allocation.  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc (device memory owned by a host framework whose
+ * allocator must account for every byte, a process under a hard memory cap,
+ * or work recorded while allocation is forbidden), who therefore cannot
+ * create a plan.
+ *   yhat, y_meas, meas_idx, r2, loss: as in sdp_residual_loss (DEVICE);
+ *   B >= 1 rows of yhat, J >= 1 samples per row, B * J <= SDP_NOALLOC_MAX_ELEMS,
+ *   larger sizes return SDP_ERR_INVALID_ARG.  Rows of meas_idx outside
+ *   [0, n_meas_rows) contribute a zero residual (there is no status word).
+ * Scratch: a fixed 32 KB + 256 B array inside the library image on every
+ * device that loads the library, held until the process exits.  The first
+ * call on a device looks its address up (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array, so calls that overlap on the GPU race: the
+ * caller serialises them.  Each call clears the completion counter before
+ * its kernel and rewrites every partial sum it reads.
+ */
+#define SDP_NOALLOC_MAX_ELEMS (1LL << 28)
+int sdp_residual_loss_noalloc(const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                              const int32_t* meas_idx, int32_t B, int64_t J, void* r2, float* loss,
+                              void* stream);
+
+/*
  * Synchronise `stream`, return the plan's device status word (SDP_OK or the
  * first device-side error recorded since the last call) and clear it.
  */
