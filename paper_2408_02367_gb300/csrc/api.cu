@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -44,6 +46,7 @@ struct sdp_plan_s {
     // device memory
     float4* pts = nullptr;
     int* tframe = nullptr;
+    float* wts = nullptr;    // [J][3W] Kaiser-Bessel weights of the sorted samples
     float2* V = nullptr;
     float2* S = nullptr;
     float* dinv = nullptr;   // [N1 | N2 | N3]
@@ -222,11 +225,19 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
         for (int a = 0; a < 3; ++a) gc[(size_t)j * 3 + a] = grid_coord(om[a], p->M[a]);
     }
 
-    // ---- bins: shape chosen so that a K-channel tile fits in 48 KB of shared memory ----
-    int bs[3] = {8, 8, 16};
-    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[2] > 4) bs[2] /= 2;
-    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[1] > 4) bs[1] /= 2;
-    while ((long long)K * bs[0] * bs[1] * bs[2] * 8 > 48 * 1024 && bs[0] > 4) bs[0] /= 2;
+    // ---- bins: 8x8x8 by default, halved along the slowest axes until a K-channel tile
+    // is at most 24 KB of shared memory (SDP_SPREAD_BIN="b1,b2,b3" overrides; b3 even) ----
+    int bs[3] = {8, 8, 8};
+    if (const char* ev = std::getenv("SDP_SPREAD_BIN")) {
+        int v[3];
+        if (std::sscanf(ev, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3 && v[0] >= 1 && v[1] >= 1 && v[2] >= 2 &&
+            v[2] % 2 == 0 && (long long)K * v[0] * v[1] * v[2] * 8 <= 160 * 1024)
+            for (int a = 0; a < 3; ++a) bs[a] = v[a];
+    } else {
+        for (int a = 0; a < 2 && (long long)K * bs[0] * bs[1] * bs[2] * 8 > 24 * 1024; ++a)
+            for (int q = 0; q < 2 && (long long)K * bs[0] * bs[1] * bs[2] * 8 > 24 * 1024; ++q)
+                if (bs[q] > 4) bs[q] /= 2;
+    }
     for (int a = 0; a < 3; ++a) {
         p->bs[a] = bs[a];
         p->nb[a] = (int)((p->M[a] + bs[a] - 1) / bs[a]);
@@ -322,7 +333,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
         }
     }
     // subproblems: every bin (empty ones too, they write zeros), chunks of at most kChunk
-    const long long kChunk = 1024;
+    long long kChunk = 512;
+    if (const char* ev = std::getenv("SDP_SPREAD_CHUNK")) kChunk = std::max(32LL, std::atoll(ev));
     std::vector<SubProb> subs;
     long long slots = 0;
     for (long long b = 0; b < nbins; ++b) {
@@ -351,6 +363,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     const size_t Kz = (size_t)K;
     SDP_TRY(dev_alloc(p, &p->pts, (size_t)J));
     SDP_TRY(dev_alloc(p, &p->tframe, (size_t)J));
+    SDP_TRY(dev_alloc(p, &p->wts, (size_t)J * 3 * W));
     SDP_TRY(dev_alloc(p, &p->V, (size_t)d->T * Kz));
     SDP_TRY(dev_alloc(p, &p->S, (size_t)d->C * nvox));
     SDP_TRY(dev_alloc(p, &p->dinv, dinv.size()));
@@ -381,6 +394,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
+    SDP_CUDA(launch_kb_weights(g, p->pts, p->wts, st));
     SDP_CUDA(cudaStreamSynchronize(st));
     size_t o = 0;
     for (int a = 0; a < 3; ++a) {
@@ -461,8 +475,8 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
         return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3, BK, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->pts, p->tframe, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y), accumulate,
-                             st);
+        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y),
+                             accumulate, st);
     }));
     return SDP_OK;
 }
@@ -475,7 +489,7 @@ int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, i
     const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
     const long long BK = (long long)B * nk;
     SDP_TRY(run(p, ST_SPREAD, st, [&] {
-        return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->V,
+        return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->wts, p->V,
                              static_cast<const float2*>(y), scale, B, k0, nk, p->bufA, p->partials, p->slots_per_b,
                              p->counters, p->nbins, st);
     }));

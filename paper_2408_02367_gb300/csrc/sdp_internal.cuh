@@ -62,7 +62,9 @@ struct Geo {
     float halfW;
 };
 
-struct Launch;   // profiling hook, defined in api.cu
+// Compile-time channel-group size of the interpolation and spread kernels for
+// nk channels: exact for 1..5, groups of 8 above.
+inline int channel_group(int nk) { return nk <= 5 ? nk : 8; }
 
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
 cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
@@ -76,17 +78,36 @@ cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int accumulate,
                                      int* status, cudaStream_t st);
-cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, const float2* V,
+// Kaiser-Bessel weights of every (sorted) sample: wts[s][d][a] = phi(g_d - (m0_d + a)),
+// m0_d = ceil(g_d - W/2) in float32; computed once per plan.
+cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaStream_t st);
+cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                           cudaStream_t st);
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
-                          const int* inc, const float4* pts, const int* tframe, const float2* V,
+                          const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
                           float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
 int residual_loss_blocks();
 cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
                                  int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
                                  int* status, cudaStream_t st);
+
+// Two-pass register FFT kernels (fft2.cu) for the specialised lengths; they
+// return cudaErrorNotSupported for any other length (the Stockham kernels of
+// fft.cu then run instead).
+bool fft2_supported(int L);
+cudaError_t launch_fft2_strided(const FftAxis& ax, int inverse, const float2* in, float2* out, int n_in,
+                                int in_centred, int n_out, int out_centred, long long inner, long long outer,
+                                cudaStream_t st);
+cudaError_t launch_fft2_fwd_prologue(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
+                                     const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                     const float* dinv2, const float* dinv3, float2* out, int* status,
+                                     cudaStream_t st);
+cudaError_t launch_fft2_adj_epilogue(const Geo& g, const FftAxis& ax, const float2* in, const float2* S,
+                                     const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                     const float* dinv2, const float* dinv3, float2* out, int accumulate,
+                                     int* status, cudaStream_t st);
 
 // Host helpers.
 bool fft_factor(int L, FftAxis* ax);

@@ -73,6 +73,12 @@ CASES = {
     "w2": ((10, 10, 10), 2, 1.25, 2, 2, 3, 1, 300, [0, 1]),
     "sigma1_w4": ((16, 16, 16), 4, 1.0, 3, 2, 5, 1, 400, [1, 0]),
     "w6_anisotropic": ((24, 16, 8), 6, 2.0, 4, 3, 10, 1, 256, [2, 1, 0]),
+    # grid lengths served by the two-pass register FFT (axis 3 = fused prologue / epilogue)
+    "fft2_160_axis3": ((8, 16, 128), 4, 1.25, 5, 2, 12, 1, 512, [1, 0]),
+    "fft2_120_80": ((96, 8, 64), 4, 1.25, 2, 2, 6, 1, 300, [0, 1]),
+    "fft2_250_axis1": ((200, 8, 10), 4, 1.25, 3, 2, 5, 1, 300, [1]),
+    "fft2_200_250": ((8, 160, 200), 4, 1.25, 2, 2, 4, 1, 300, [0, 1]),
+    "fft2_240_256": ((120, 8, 128), 4, 2.0, 1, 1, 3, 1, 200, [0]),
 }
 
 
@@ -98,6 +104,33 @@ def test_forward_and_adjoint_match_oracle(name):
         assert ea < SIGMA1_ADJ_BOUND
     else:
         assert ea < stated_tol(W, sigma) and ea < FP32_BOUND
+
+
+def test_generic_fft_engine_matches_oracle(tmp_path):
+    """The Stockham fallback (forced by SDP_FFT_GENERIC=1 in a child process) on a
+    length the two-pass engine normally serves."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, sys\n"
+        "sys.path.insert(0, '.')\n"
+        "from tests.test_gpu_parity import make_case, gpu_op, t, rel, FP32_BOUND\n"
+        "from oracle import nufft as O\n"
+        "c = make_case((8, 16, 128), 4, 1.25, 3, 2, 6, 1, 300, [1, 0])\n"
+        "geo = O.Geometry(c['n'], 4, 1.25)\n"
+        "A = gpu_op(c)\n"
+        "y = A.forward(t(c['x']), t(c['coils'])).cpu().numpy()\n"
+        "e = rel(y, O.gridding_forward(geo, c['x'], c['S'], c['V'], c['omega'], c['frame'], c['coils']))\n"
+        "r = np.ascontiguousarray(y)\n"
+        "a = A.adjoint(t(r), t(c['coils'])).cpu().numpy()\n"
+        "ea = rel(a, O.gridding_adjoint(geo, r, c['S'], c['V'], c['omega'], c['frame'], c['coils']))\n"
+        "print(e, ea)\n"
+        "assert e < FP32_BOUND and ea < FP32_BOUND\n")
+    import os
+    env = dict(os.environ, SDP_FFT_GENERIC="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
 
 
 def test_adjoint_identity_on_gpu():
