@@ -225,19 +225,9 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
         for (int a = 0; a < 3; ++a) gc[(size_t)j * 3 + a] = grid_coord(om[a], p->M[a]);
     }
 
-    // ---- bins: 8x8x8 by default, halved along the slowest axes until a K-channel tile
-    // is at most 24 KB of shared memory (SDP_SPREAD_BIN="b1,b2,b3" overrides; b3 even) ----
-    int bs[3] = {8, 8, 8};
-    if (const char* ev = std::getenv("SDP_SPREAD_BIN")) {
-        int v[3];
-        if (std::sscanf(ev, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3 && v[0] >= 1 && v[1] >= 1 && v[2] >= 2 &&
-            v[2] % 2 == 0 && (long long)K * v[0] * v[1] * v[2] * 8 <= 160 * 1024)
-            for (int a = 0; a < 3; ++a) bs[a] = v[a];
-    } else {
-        for (int a = 0; a < 2 && (long long)K * bs[0] * bs[1] * bs[2] * 8 > 24 * 1024; ++a)
-            for (int q = 0; q < 2 && (long long)K * bs[0] * bs[1] * bs[2] * 8 > 24 * 1024; ++q)
-                if (bs[q] > 4) bs[q] /= 2;
-    }
+    // ---- bins: 8 x 4 x 8 grid points (one warp of the spread, a lane per axis-3
+    // column of 8 points held in registers) ----
+    int bs[3] = {8, 4, 8};
     for (int a = 0; a < 3; ++a) {
         p->bs[a] = bs[a];
         p->nb[a] = (int)((p->M[a] + bs[a] - 1) / bs[a]);
@@ -372,7 +362,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_TRY(dev_alloc(p, &p->subs, subs.size()));
     const size_t P = (size_t)bs[0] * bs[1] * bs[2];
     SDP_TRY(dev_alloc(p, &p->partials, (size_t)std::max(slots, 1LL) * P * Kz * p->maxB));
-    SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB));
+    SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB * ((K + 7) / 8)));
     SDP_TRY(dev_alloc(p, &p->status, 1));
     SDP_TRY(dev_alloc(p, &p->loss_partials, (size_t)residual_loss_blocks()));
     SDP_TRY(dev_alloc(p, &p->loss_counter, 1));
@@ -391,7 +381,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_CUDA(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->inc, inc.data(), inc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(SubProb), cudaMemcpyHostToDevice, st));
-    SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * sizeof(int), st));
+    SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * ((K + 7) / 8) * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
     SDP_CUDA(launch_kb_weights(g, p->pts, p->wts, st));
