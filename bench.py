@@ -380,13 +380,32 @@ def run_native(args):
         pass
     clocks = ClockSampler(gpu_id).start()
     total_ms, launches, prof = timed(dip_step, args.steps, args.warmup, True)
-    clk = clocks.stop()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     total_ms = max_over_ranks(total_ms, dist, dev)
     ms = total_ms / args.steps
-    value = ws * B * w.J / (ms * 1e-3)
+
+    # ---- the same step captured once in a CUDA graph and replayed ----
+    from paper_2408_02367_gb300 import graph as sdp_graph
+    gstep = sdp_graph.DipStepGraph(A, y_meas, torch.from_numpy(x_hat).to(dev), B)
+    for i in range(args.warmup):
+        flush.fill_(0.0)
+        gstep.step(coil_dev[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        gev[i][0].record()
+        gstep.step(coil_dev[args.warmup + i])
+        gev[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()      # sampled over both timed regions (eager and graph)
+    graph_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in gev), dist, dev) / args.steps
+    graph_launches = gstep.launches_per_step * args.steps
+    del gstep
 
     # ---- plain form, same draws, fewer steps ----
     n_plain = min(args.steps, 20)
@@ -453,27 +472,33 @@ def run_native(args):
     if rank != 0:
         return 0
     model = path_model_bytes(w, B, M)
+    # headline: the step as a training loop runs it, captured in a CUDA graph
+    best_ms = graph_ms
+    value = ws * B * w.J / (best_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": best_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_desc(w, B), "grid": list(M), "l2": "flushed between steps "
-                   f"({FLUSH_BYTES >> 20} MiB write outside the timed events)", "parallelism":
+                   f"({FLUSH_BYTES >> 20} MiB write outside the timed events)", "timed": "CUDA-graph replay "
+                   "of the whole step (eager step reported in dip_step_ms)", "parallelism":
                    "replicas" if ws > 1 else "single GPU", "coil_draws": "uniform without replacement, "
                    "pre-drawn and resident on the device"},
-        "dip_step_ms": ms,
+        "dip_step_ms": {"eager": ms, "cuda_graph": graph_ms},
         "plain_form": {"ms_per_step": plain_ms, "launches_per_step": plain_launches / n_plain,
-                       "rel_err_vs_plain": rel_vs_plain, "speedup": plain_ms / ms},
+                       "rel_err_vs_plain": rel_vs_plain, "speedup_vs_eager": plain_ms / ms,
+                       "speedup_vs_graph": plain_ms / graph_ms},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
                      "alg_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
-        "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (ms * 1e-3)},
+        "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},
         "cpu_baseline": cpu,
         "e2e": {"value": ws * B * w.J / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3, "steps": n_e2e},
-        "gpu_launches": launches,
+        "gpu_launches": graph_launches,
+        "gpu_launches_eager_region": launches,
         "clocks": clk,
     }
     print(json.dumps(line))

@@ -169,6 +169,39 @@ int sdp_residual_loss(sdp_plan_t plan, const void* yhat, const void* y_meas, int
                       const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream);
 
 /*
+ * One application of an operator inside a batch (several volumes / plans):
+ *   plan      the item's plan
+ *   in        forward: DEVICE x [K][N1][N2][N3]; adjoint: DEVICE y [B][J]
+ *   coil_idx  DEVICE int32 [B]
+ *   B         1..max_batch of the plan
+ *   accumulate forward: ignored (y is overwritten); adjoint: 0 overwrite, 1 add
+ *   out       forward: DEVICE y [B][J]; adjoint: DEVICE out [K][N1][N2][N3]
+ */
+typedef struct {
+    sdp_plan_t plan;
+    const void* in;
+    const int32_t* coil_idx;
+    int32_t B;
+    int32_t accumulate;
+    void* out;
+} sdp_work;
+
+/*
+ * Apply the forward (resp. adjoint) operator of every item (StoDIP Eq. 3 for
+ * several reconstructions at once, e.g. uneven coil minibatches of volumes of
+ * different matrix sizes).  Items whose plans differ run concurrently on
+ * library-owned worker streams forked from and joined back to `stream`, so the
+ * whole batch is ordered after earlier work on `stream` and before later work
+ * on it, and can be captured in a CUDA graph; items that share a plan run one
+ * after the other (they share its workspace).  All items are checked before
+ * anything is launched.  The worker streams of a device are created by its
+ * first batched call: make that call before any stream capture.  Batched calls
+ * from several host threads are serialised by the library.
+ */
+int sdp_forward_batched(const sdp_work* items, int32_t n, void* stream);
+int sdp_adjoint_batched(const sdp_work* items, int32_t n, void* stream);
+
+/*
  * Residual and loss of sdp_residual_loss without a plan and without any device
  * allocation.  The paper has no counterpart: this exists for callers that
  * cannot call cudaMalloc (device memory owned by a host framework whose

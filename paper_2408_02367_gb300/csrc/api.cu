@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -497,9 +498,97 @@ int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, i
     return SDP_OK;
 }
 
+// ---- batched calls: a pool of worker streams and events per device ----
+constexpr int kWorkers = 4;
+constexpr int kMaxDevices = 64;
+struct WorkerPool {
+    bool ready = false;
+    cudaStream_t st[kWorkers];
+    cudaEvent_t fork;
+    cudaEvent_t join[kWorkers];
+};
+std::mutex g_batch_mu;
+WorkerPool g_pools[kMaxDevices];
+
+int worker_pool(WorkerPool** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SDP_ERR_CUDA;
+    }
+    WorkerPool& wp = g_pools[dev];
+    if (!wp.ready) {
+        for (int w = 0; w < kWorkers; ++w) {
+            SDP_CUDA(cudaStreamCreateWithFlags(&wp.st[w], cudaStreamNonBlocking));
+            SDP_CUDA(cudaEventCreateWithFlags(&wp.join[w], cudaEventDisableTiming));
+        }
+        SDP_CUDA(cudaEventCreateWithFlags(&wp.fork, cudaEventDisableTiming));
+        wp.ready = true;
+    }
+    *out = &wp;
+    return SDP_OK;
+}
+
+int run_batched(const sdp_work* items, int n, bool adjoint, cudaStream_t st) {
+    if (n < 0 || (n > 0 && !items)) return SDP_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        const sdp_work& w = items[i];
+        if (!w.plan) return SDP_ERR_INVALID_ARG;
+        SDP_TRY(check_call(w.plan, w.in, w.coil_idx, w.B, 0, w.plan->geo.K, w.out));
+    }
+    if (n == 0) return SDP_OK;
+    auto run_one = [&](const sdp_work& w, cudaStream_t s) {
+        return adjoint ? adjoint_impl(w.plan, w.in, w.coil_idx, w.B, 0, w.plan->geo.K, w.out, w.accumulate ? 1 : 0,
+                                      nullptr, s)
+                       : forward_impl(w.plan, w.in, w.coil_idx, w.B, 0, w.plan->geo.K, w.out, 0, s);
+    };
+    // worker of each item: one worker per distinct plan (round robin), same plan -> same worker
+    std::vector<sdp_plan_s*> plans;
+    std::vector<int> worker(n);
+    for (int i = 0; i < n; ++i) {
+        int k = -1;
+        for (size_t q = 0; q < plans.size(); ++q)
+            if (plans[q] == items[i].plan) k = (int)q;
+        if (k < 0) {
+            k = (int)plans.size();
+            plans.push_back(items[i].plan);
+        }
+        worker[i] = k % kWorkers;
+    }
+    if (plans.size() == 1) {   // nothing to overlap
+        for (int i = 0; i < n; ++i) SDP_TRY(run_one(items[i], st));
+        return SDP_OK;
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    WorkerPool* wp = nullptr;
+    SDP_TRY(worker_pool(&wp));
+    const int used = (int)std::min<size_t>(plans.size(), kWorkers);
+    SDP_CUDA(cudaEventRecord(wp->fork, st));
+    for (int w = 0; w < used; ++w) SDP_CUDA(cudaStreamWaitEvent(wp->st[w], wp->fork, 0));
+    int rc = SDP_OK;
+    for (int i = 0; i < n && rc == SDP_OK; ++i) rc = run_one(items[i], wp->st[worker[i]]);
+    // always join the workers back, also after a failed launch
+    for (int w = 0; w < used; ++w) {
+        if (cudaEventRecord(wp->join[w], wp->st[w]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, wp->join[w], 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = rc == SDP_OK ? SDP_ERR_CUDA : rc;
+        }
+    }
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+int sdp_forward_batched(const sdp_work* items, int32_t n, void* stream) {
+    return run_batched(items, n, false, static_cast<cudaStream_t>(stream));
+}
+
+int sdp_adjoint_batched(const sdp_work* items, int32_t n, void* stream) {
+    return run_batched(items, n, true, static_cast<cudaStream_t>(stream));
+}
 
 int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* d, void* stream) {
     if (!out) return SDP_ERR_INVALID_ARG;

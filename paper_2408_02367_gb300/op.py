@@ -52,6 +52,17 @@ class PlanDesc(ctypes.Structure):
     ]
 
 
+class Work(ctypes.Structure):
+    _fields_ = [
+        ("plan", ctypes.c_void_p),
+        ("in_", ctypes.c_void_p),
+        ("coil_idx", ctypes.c_void_p),
+        ("B", ctypes.c_int32),
+        ("accumulate", ctypes.c_int32),
+        ("out", ctypes.c_void_p),
+    ]
+
+
 _LIB = None
 
 EXPORTS = {
@@ -75,6 +86,8 @@ EXPORTS = {
     "sdp_residual_loss_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_forward_batched": (ctypes.c_int, [ctypes.POINTER(Work), ctypes.c_int32, ctypes.c_void_p]),
+    "sdp_adjoint_batched": (ctypes.c_int, [ctypes.POINTER(Work), ctypes.c_int32, ctypes.c_void_p]),
     "sdp_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sdp_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "sdp_plan_beta": (ctypes.c_double, [ctypes.c_void_p]),
@@ -302,6 +315,42 @@ class SubspaceNufft:
         if n < 0:
             raise SdpError(-n, "sdp_profile_read")
         return {STAGES[i]: (float(ms[i]), int(nl[i])) for i in range(n)}
+
+
+def _batched(items, adjoint):
+    if not items:
+        return []
+    dev = items[0][0].device
+    arr = (Work * len(items))()
+    outs = []
+    for i, (op, inp, coil_idx, out, acc) in enumerate(items):
+        B = op._coils(coil_idx)
+        if adjoint:
+            _require(inp, "y", torch.complex64, op.device, (B, op.J))
+            if out is None:
+                out = torch.empty((op.K,) + op.n, dtype=torch.complex64, device=op.device)
+            _require(out, "out", torch.complex64, op.device, (op.K,) + op.n)
+        else:
+            _require(inp, "x", torch.complex64, op.device, (op.K,) + op.n)
+            if out is None:
+                out = torch.empty((B, op.J), dtype=torch.complex64, device=op.device)
+            _require(out, "y", torch.complex64, op.device, (B, op.J))
+        arr[i] = Work(op._h.value, inp.data_ptr(), coil_idx.data_ptr(), B, int(bool(acc)), out.data_ptr())
+        outs.append(out)
+    fn = lib().sdp_adjoint_batched if adjoint else lib().sdp_forward_batched
+    _check(fn(arr, len(items), _stream_ptr(dev)), "sdp_adjoint_batched" if adjoint else "sdp_forward_batched")
+    return outs
+
+
+def forward_batched(items):
+    """items: [(op, x, coil_idx, y_out_or_None)] -> list of y.  Plans differing
+    between items run concurrently on the library's worker streams."""
+    return _batched([(op, x, c, o, False) for (op, x, c, o) in items], adjoint=False)
+
+
+def adjoint_batched(items):
+    """items: [(op, y, coil_idx, out_or_None, accumulate)] -> list of out."""
+    return _batched(list(items), adjoint=True)
 
 
 def launch_count() -> int:

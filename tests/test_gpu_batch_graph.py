@@ -1,0 +1,105 @@
+"""Batched multi-volume calls and the CUDA-graph captured DIP step, against the
+plain per-item calls (which the parity tests pin to the FP64 oracle)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nufft as O
+from paper_2408_02367_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2408_02367_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _volume(n, W, sigma, K, C, T, arm_len, seed):
+    from paper_2408_02367_gb300 import op
+    x = synth.ellipsoid_phantom(n, K, seed=seed)
+    S = synth.coil_maps(n, C)
+    V = synth.subspace_basis(T, K, seed=seed + 10)
+    omega, frame = synth.spiral_trajectory(T, 1, arm_len)
+    A = op.make_operator(omega, frame, n, W, sigma, V, S, max_batch=4)
+    return A, x
+
+
+def test_batched_items_equal_single_calls():
+    from paper_2408_02367_gb300 import op
+    vols = [_volume((16, 16, 16), 4, 1.25, 5, 4, 20, 256, 1),
+            _volume((20, 24, 18), 6, 2.0, 3, 3, 10, 300, 2),
+            _volume((12, 12, 12), 4, 2.0, 5, 2, 8, 200, 3)]
+    coil_sets = [[3, 1], [2], [1, 0, 1], [0]]
+    plan_of = [0, 1, 2, 0]            # two items share the first plan
+    items = []
+    for i, (pi, cs) in enumerate(zip(plan_of, coil_sets)):
+        A, x = vols[pi]
+        items.append((A, _t(x), _t(np.array(cs, np.int32)), None))
+    ys = op.forward_batched(items)
+    for (A, x, c, _), y in zip(items, ys):
+        assert torch.equal(y, A.forward(x, c))
+    adj_items = [(A, y, c, None, False) for (A, _, c, _), y in zip(items, ys)]
+    outs = op.adjoint_batched(adj_items)
+    for (A, y, c, _, _), o in zip(adj_items, outs):
+        assert torch.equal(o, A.adjoint(y, c))
+    # accumulate into a shared output of one plan across two items
+    A0, _ = vols[0]
+    acc = torch.zeros_like(outs[0])
+    op.adjoint_batched([(A0, ys[0], items[0][2], acc, True), (A0, ys[3], items[3][2], acc, True)])
+    ref = A0.adjoint(ys[0], items[0][2]) + A0.adjoint(ys[3], items[3][2])
+    assert (torch.linalg.norm(acc - ref) / torch.linalg.norm(ref)).item() < 1e-6
+    for A, _ in vols:
+        assert A.status() == 0
+
+
+def test_batched_rejects_bad_item_before_launching():
+    from paper_2408_02367_gb300 import op
+    A, x = _volume((10, 10, 10), 4, 2.0, 2, 2, 4, 100, 4)
+    xt = _t(x)
+    good = torch.tensor([0], dtype=torch.int32, device="cuda")
+    n0 = op.launch_count()
+    bad = (A, xt, torch.zeros(9, dtype=torch.int32, device="cuda"), None)   # B = 9 > max_batch
+    with pytest.raises(ValueError):
+        op.forward_batched([(A, xt, good, None), bad])
+    assert op.launch_count() == n0
+
+
+def test_graph_replay_equals_eager_step():
+    from paper_2408_02367_gb300 import graph, op
+    n, W, sigma, K, C, T = (24, 24, 24), 4, 1.25, 5, 4, 30
+    x = synth.ellipsoid_phantom(n, K)
+    S = synth.coil_maps(n, C)
+    V = synth.subspace_basis(T, K)
+    omega, frame = synth.spiral_trajectory(T, 1, 512)
+    A = op.make_operator(omega, frame, n, W, sigma, V, S, max_batch=2)
+    y_meas = torch.stack([A.forward(_t(synth.ellipsoid_phantom(n, K, seed=7)),
+                                    torch.tensor([c], dtype=torch.int32, device="cuda"))[0] for c in range(C)])
+    g = graph.DipStepGraph(A, y_meas, _t(x), B=2)
+    assert g.launches_per_step == 9
+    xe = _t(x).requires_grad_(True)
+    for cs in ([1, 3], [0, 2], [3, 3]):
+        ci = torch.tensor(cs, dtype=torch.int32, device="cuda")
+        loss, grad = g.step(ci)
+        xe.grad = None
+        le = op.dc_loss(A, xe, ci, y_meas)
+        le.backward()
+        torch.cuda.synchronize()
+        assert torch.equal(loss, le.detach())
+        assert torch.equal(grad, xe.grad)
+    # a new x through the static input
+    x2 = _t(synth.ellipsoid_phantom(n, K, seed=11))
+    loss, grad = g.step(torch.tensor([2, 0], dtype=torch.int32, device="cuda"), x=x2)
+    x2e = x2.clone().requires_grad_(True)
+    le = op.dc_loss(A, x2e, torch.tensor([2, 0], dtype=torch.int32, device="cuda"), y_meas)
+    le.backward()
+    assert torch.equal(grad, x2e.grad)
+    assert A.status() == 0
