@@ -265,6 +265,18 @@ int64_t sdp_launch_count(void);
 int sdp_profile_enable(sdp_plan_t plan, int32_t enable);
 int sdp_profile_read(sdp_plan_t plan, double* ms, int64_t* launches, int32_t cap);
 
+/*
+ * Host-only helpers (no device, no plan), for callers that size buffers:
+ *   sdp_grid_size: the oversampled grid length a plan uses for an axis of n
+ *                  voxels, the smallest even 2,3,5-smooth M >= max(ceil(sigma n), 2W);
+ *                  -1 for n < 1, W outside 2..8 or sigma outside [1, 4].
+ *   sdp_kb_beta:   the Kaiser-Bessel shape parameter of width W and oversampling
+ *                  sigma, pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8) (Beatty et al.
+ *                  2005); -1 when the square root's argument is not positive.
+ */
+int64_t sdp_grid_size(int64_t n, double oversamp, int32_t width);
+double sdp_kb_beta(int32_t width, double oversamp);
+
 /* Static text for a status code. */
 const char* sdp_strerror(int status);
 

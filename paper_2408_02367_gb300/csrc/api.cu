@@ -728,6 +728,16 @@ int sdp_profile_read(sdp_plan_t p, double* ms, int64_t* launches, int32_t cap) {
     return n;
 }
 
+int64_t sdp_grid_size(int64_t n, double oversamp, int32_t width) {
+    if (n < 1 || width < 2 || width > kMaxWidth || !(oversamp >= 1.0 && oversamp <= 4.0)) return -1;
+    return grid_len(n, oversamp, width);
+}
+
+double sdp_kb_beta(int32_t width, double oversamp) {
+    const double arg = (width / oversamp) * (width / oversamp) * (oversamp - 0.5) * (oversamp - 0.5) - 0.8;
+    return arg > 0 ? kPi * std::sqrt(arg) : -1.0;
+}
+
 const char* sdp_strerror(int s) {
     switch (s) {
         case SDP_OK: return "ok";

@@ -97,6 +97,8 @@ EXPORTS = {
     "sdp_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "sdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sdp_grid_size": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_double, ctypes.c_int32]),
+    "sdp_kb_beta": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double]),
 }
 
 

@@ -1,0 +1,75 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point
+that include/stodip_op.h declares; host-only entry points answer correctly."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import nufft as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stodip_op.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_02367_gb300 import build, op
+    build.build()
+    return op.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ["sdp_plan_create", "sdp_plan_destroy", "sdp_forward", "sdp_adjoint", "sdp_forward_batched",
+                 "sdp_adjoint_batched", "sdp_status", "sdp_workspace_bytes", "sdp_strerror",
+                 "sdp_residual_loss", "sdp_adjoint_scaled"]:
+        assert need in names
+
+
+def test_every_declared_function_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_2408_02367_gb300 import op
+    assert set(op.EXPORTS) <= set(declared_functions())
+
+
+def test_status_strings_and_counters_without_gpu(lib):
+    for code in range(7):
+        assert lib.sdp_strerror(code)
+    assert lib.sdp_launch_count() >= 0
+    assert lib.sdp_workspace_bytes(None) == 0
+    assert lib.sdp_plan_beta(None) == -1.0
+
+
+def test_plan_create_rejects_bad_arguments_on_the_host(lib):
+    from paper_2408_02367_gb300 import op
+    h = ctypes.c_void_p(1234)
+    assert lib.sdp_plan_create(ctypes.byref(h), None, None) == 1
+    assert h.value is None
+    d = op.PlanDesc()
+    d.n = (ctypes.c_int64 * 3)(16, 16, 1)       # N3 < 2
+    assert lib.sdp_plan_create(ctypes.byref(h), ctypes.byref(d), None) == 1
+    assert lib.sdp_forward(None, None, None, 1, None, None) == 1
+    assert lib.sdp_forward_batched(None, 0, None) == 0
+    assert lib.sdp_residual_loss_noalloc(None, None, 1, None, 1, 1, None, None, None) == 1
+
+
+@pytest.mark.parametrize("n,sigma,W", [(32, 2.0, 6), (128, 1.25, 4), (200, 1.25, 4), (160, 1.25, 4),
+                                       (14, 2.0, 6), (3, 2.0, 8), (97, 1.5, 5), (24, 1.0, 4)])
+def test_grid_size_and_beta_agree_with_the_oracle(lib, n, sigma, W):
+    assert lib.sdp_grid_size(n, sigma, W) == O.grid_size(n, sigma, W)
+    assert abs(lib.sdp_kb_beta(W, sigma) - O.beatty_beta(W, sigma)) < 1e-12
+
+
+def test_grid_size_rejects_out_of_range(lib):
+    assert lib.sdp_grid_size(0, 2.0, 4) == -1
+    assert lib.sdp_grid_size(10, 0.5, 4) == -1
+    assert lib.sdp_grid_size(10, 2.0, 9) == -1
+    assert lib.sdp_kb_beta(2, 1.0) > 0 or lib.sdp_kb_beta(2, 1.0) == -1.0
