@@ -1,0 +1,122 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (128^3 image, K=5, C=8, B=2, J=491,520, W=4, sigma=1.25; and the
+200x200x160, C=32, B=8, J=2,048,000 whole-brain workload).
+
+The oracle cannot afford every output at these sizes, so:
+  - forward: a seeded sample of output k-space points, evaluated by the oracle
+    one by one (its own deapodisation, FFT of the grid and W^3 interpolation);
+  - adjoint at 128^3: every voxel (oracle spread + inverse FFT + crop);
+  - adjoint at 200x200x160: the adjoint identity <A x, y> = <x, A^H y>, which
+    holds at any size;
+  - repeatability: two identical calls give identical bits (no atomics in the
+    data path).
+Tolerance: FP32_BOUND = 2e-5 relative L2 (the stated bound at W=4 is 2e-3).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nufft as O
+from paper_2408_02367_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+FP32_BOUND = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2408_02367_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def oracle_forward_samples(geo, x, S, V, omega, frame, coil, sel):
+    """Oracle y[j] of one coil at the sample indices `sel` only."""
+    K = x.shape[0]
+    U = np.stack([O.fwd_fft(O.fwd_prologue(geo, x[k], S[coil])) for k in range(K)])
+    g32 = O.grid_coords(omega[sel], geo.M)
+    return O.fwd_interp(geo, U, V, g32, frame[sel])
+
+
+@pytest.fixture(scope="module")
+def vol128():
+    from paper_2408_02367_gb300 import op
+    w = synth.WORKLOADS["vol128_w4"]
+    x, S, V, omega, frame = synth.make_problem(w)
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=w.batch)
+    geo = O.Geometry(w.n, w.width, w.oversamp)
+    return w, A, geo, x, S, V, omega, frame
+
+
+def test_vol128_forward_sampled_outputs(vol128):
+    w, A, geo, x, S, V, omega, frame = vol128
+    coils = np.array([6, 3], np.int32)
+    y = A.forward(_t(x), _t(coils)).cpu().numpy()
+    sel = np.sort(np.random.default_rng(0).choice(w.J, size=3000, replace=False))
+    for b, c in enumerate(coils):
+        ref = oracle_forward_samples(geo, x, S, V, omega, frame, int(c), sel)
+        e = rel(y[b, sel], ref)
+        print(f"vol128 forward coil {c}: rel {e:.2e}")
+        assert e < FP32_BOUND
+
+
+def test_vol128_adjoint_all_voxels(vol128):
+    w, A, geo, x, S, V, omega, frame = vol128
+    coils = np.array([1, 5], np.int32)
+    r = synth.random_complex((2, w.J), 17)
+    a = A.adjoint(_t(r), _t(coils)).cpu().numpy()
+    ref = O.gridding_adjoint(geo, r, S, V, omega, frame, coils)
+    e = rel(a, ref)
+    print(f"vol128 adjoint: rel {e:.2e}")
+    assert e < FP32_BOUND
+
+
+def test_vol128_repeatable_bits(vol128):
+    w, A, geo, x, S, V, omega, frame = vol128
+    ci = _t(np.array([2, 7], np.int32))
+    xt = _t(x)
+    y1 = A.forward(xt, ci)
+    y2 = A.forward(xt, ci)
+    assert torch.equal(y1, y2)
+    a1 = A.adjoint(y1, ci)
+    a2 = A.adjoint(y1, ci)
+    assert torch.equal(a1, a2)
+    assert A.status() == 0
+
+
+def test_vol200_batch8_forward_sampled_and_adjoint_identity():
+    from paper_2408_02367_gb300 import op
+    w = synth.WORKLOADS["vol200_w4"]
+    x, S, V, omega, frame = synth.make_problem(w)
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8)
+    geo = O.Geometry(w.n, w.width, w.oversamp)
+    assert A.grid == (250, 250, 200)
+    coils = np.array([0, 5, 9, 14, 18, 23, 27, 31], np.int32)
+    xt = _t(x)
+    ci = _t(coils)
+    y = A.forward(xt, ci)
+    sel = np.sort(np.random.default_rng(1).choice(w.J, size=2000, replace=False))
+    yc = y.cpu().numpy()
+    for b in (0, 6):                                   # two of the eight batch entries
+        ref = oracle_forward_samples(geo, x, S, V, omega, frame, int(coils[b]), sel)
+        e = rel(yc[b, sel], ref)
+        print(f"vol200 forward coil {coils[b]}: rel {e:.2e}")
+        assert e < FP32_BOUND
+    r = _t(synth.random_complex((8, w.J), 23))
+    AHr = A.adjoint(r, ci)
+    lhs = torch.vdot(r.flatten().to(torch.complex128), y.flatten().to(torch.complex128))
+    rhs = torch.vdot(AHr.flatten().to(torch.complex128), xt.flatten().to(torch.complex128))
+    ident = abs(complex(lhs - rhs)) / abs(complex(lhs))
+    print(f"vol200 adjoint identity: {ident:.2e}")
+    assert ident < 1e-5
+    assert A.status() == 0
