@@ -175,6 +175,33 @@ def stage_bytes(w, B, M, ninc):
     }
 
 
+# DRAM bytes (read + write) of one launch of each kernel on the vol128_w4
+# workload (B=2, K=5), from one `ncu --set full` capture each (profiles/
+# kernels_vol128_w4.md), keyed with a hash of the kernel's source file at
+# capture time: a kernel whose source has changed since reports null.
+NCU_TRAFFIC = {
+    "spread": ("spread.cu", "90685e46715758ca", (95.634688 + 305.033728) * 1e6),
+    "interp": ("interp.cu", "c361be2ea2ecdce8", (242.524672 + 8.102144) * 1e6),
+    "fwd_prologue_fft3": ("fft2.cu", "1b4f0646957d9724", (117.494016 + 156.42752) * 1e6),
+    "adj_ifft3_epilogue": ("fft2.cu", "1b4f0646957d9724", (243.298304 + 62.400768) * 1e6),
+}
+
+
+def source_hash(fname):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2408_02367_gb300", "csrc", fname)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(stage, workload_name, B):
+    """ncu DRAM bytes per launch of `stage`, if captured for this workload and the current source."""
+    if workload_name != "vol128_w4" or B != 2 or stage not in NCU_TRAFFIC:
+        return None
+    fname, h, nbytes = NCU_TRAFFIC[stage]
+    return nbytes if source_hash(fname) == h else None
+
+
 def path_model_bytes(w, B, M):
     """Whole-step model: 8 K Nvox + B (8 Nvox + 16 K G + 8 J) + 12 J per direction."""
     nvox = int(np.prod(w.n))
@@ -489,7 +516,8 @@ def run_native(args):
                        "rel_err_vs_plain": rel_vs_plain, "speedup_vs_eager": plain_ms / ms,
                        "speedup_vs_graph": plain_ms / graph_ms},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": measured_traffic(dom, w.name, B),
                      "alg_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
