@@ -486,7 +486,9 @@ def run_native(args):
     stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     dom = max(stages, key=lambda k: stages[k]["ms_total"])
     avg_ms = stages[dom]["ms_total"] / stages[dom]["launches"]
-    achieved = sb[dom] / (avg_ms * 1e-3) / 1e9
+    per_step = stages[dom]["launches"] / args.steps          # launches of this stage in one step
+    bytes_per_launch = sb[dom] / per_step
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     step_share = {k: round(v["ms_total"] / sum(s["ms_total"] for s in stages.values()), 4) for k, v in stages.items()}
 
     cpu = None
@@ -518,7 +520,8 @@ def run_native(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
                      "traffic": measured_traffic(dom, w.name, B),
-                     "alg_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms},
+                     "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                     "launches_per_step": per_step},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
         "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},

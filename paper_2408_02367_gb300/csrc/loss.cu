@@ -6,72 +6,96 @@
 // and the gradient of L with respect to yhat in PyTorch's convention,
 // dL/dRe + i dL/dIm = 2 r, which the adjoint consumes in loss.backward().
 //
-// One pass over the residual: every thread accumulates |r|^2 in float64,
-// blocks reduce in shared memory and write one partial each; the last block
-// to finish (device-scope counter, no waiting) sums the partials in block
-// order, so the loss is bitwise repeatable.
+// One pass over the residual: a block per 1024 entries of one row, every
+// thread accumulates |r|^2 in float64, blocks reduce in a fixed order and write
+// one partial each; the last block to finish (device-scope counter, no
+// waiting) sums the partials in a fixed order, so the loss is bitwise
+// repeatable.
 #include "sdp_internal.cuh"
 
 namespace sdp {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPerThread = 4;                       // residual entries per thread
+constexpr int kPerBlock = kThreads * kPerThread;    // one block covers 1024 entries of one row
 
+// Fixed-order block reduction of a double (warp butterflies, then warps in order).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    return s;   // valid in thread 0
+}
+
+// grid = (ceil(J / 1024), B): block (x, b) handles entries [1024 x, 1024 x + 1024) of row b.
 __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
     const float2* yhat, const float2* __restrict__ ymeas, const int* __restrict__ meas_idx,
-    int B, long long J, int nrows, float2* r2, double* __restrict__ partials,
+    long long J, int nrows, float2* r2, double* __restrict__ partials,
     unsigned int* __restrict__ counter, float* __restrict__ loss, int* status) {
     __shared__ double red[kThreads / 32];
     __shared__ bool s_last;
+    const int b = blockIdx.y;
+    const int row = __ldg(meas_idx + b);
+    const bool ok = row >= 0 && row < nrows;
+    if (!ok && threadIdx.x == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
+    const float2* h = yhat + (long long)b * J;
+    const float2* m = ymeas + (long long)(ok ? row : 0) * J;
+    float2* o = r2 + (long long)b * J;
+    const long long j0 = (long long)blockIdx.x * kPerBlock;
     double acc = 0.0;
-    const long long total = (long long)B * J;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e / J);
-        const long long j = e - (long long)b * J;
-        const int row = __ldg(meas_idx + b);
-        float2 r;
-        if (row >= 0 && row < nrows) {
-            const float2 h = yhat[e];
-            const float2 m = __ldg(ymeas + (long long)row * J + j);
-            r = make_float2(h.x - m.x, h.y - m.y);
-        } else {
-            if (status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
-            r = make_float2(0.f, 0.f);
+    // consecutive threads take consecutive entries: each pass of the block is one
+    // coalesced 2 KB read of yhat and of y_meas
+#pragma unroll
+    for (int u = 0; u < kPerThread; ++u) {
+        const long long j = j0 + u * kThreads + threadIdx.x;
+        if (j < J) {
+            float2 r = make_float2(0.f, 0.f);
+            if (ok) {
+                const float2 hv = h[j];
+                const float2 mv = __ldg(m + j);
+                r = make_float2(hv.x - mv.x, hv.y - mv.y);
+            }
+            acc += (double)r.x * r.x + (double)r.y * r.y;
+            o[j] = make_float2(2.f * r.x, 2.f * r.y);
         }
-        acc += (double)r.x * r.x + (double)r.y * r.y;
-        r2[e] = make_float2(2.f * r.x, 2.f * r.y);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const double bs = block_sum(acc, red);
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-        partials[blockIdx.x] = s;
+        partials[bid] = bs;
         __threadfence();
-        const unsigned prev = atomicAdd(counter, 1u);
-        s_last = (prev == gridDim.x - 1);
+        s_last = (atomicAdd(counter, 1u) == nblk - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        double s = 0.0;
-        for (unsigned i = 0; i < gridDim.x; ++i) s += __ldcg(partials + i);
-        *loss = (float)s;
+    if (!s_last) return;
+    // last block: every thread sums a fixed strided subset, then the fixed-order block sum
+    __threadfence();
+    double v = 0.0;
+    for (unsigned i = threadIdx.x; i < nblk; i += kThreads) v += __ldcg(partials + i);
+    const double tot = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        *loss = (float)tot;
         *counter = 0u;
     }
 }
 
 }  // namespace
 
-int residual_loss_blocks() { return 2 * 152; }
+long long residual_loss_partials(int maxB, long long J) { return (long long)maxB * ((J + kPerBlock - 1) / kPerBlock); }
 
 cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
                                  int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
                                  int* status, cudaStream_t st) {
-    residual_loss_kernel<<<residual_loss_blocks(), kThreads, 0, st>>>(yhat, ymeas, meas_idx, B, J, nrows, r2,
-                                                                     partials, counter, loss, status);
+    const long long nx = (J + kPerBlock - 1) / kPerBlock;
+    if (nx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)nx, (unsigned)B);
+    residual_loss_kernel<<<grid, kThreads, 0, st>>>(yhat, ymeas, meas_idx, J, nrows, r2, partials, counter, loss,
+                                                    status);
     return cudaGetLastError();
 }
 

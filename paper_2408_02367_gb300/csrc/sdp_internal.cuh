@@ -88,7 +88,7 @@ cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const 
                           const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
                           float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
-int residual_loss_blocks();
+long long residual_loss_partials(int maxB, long long J);
 cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
                                  int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
                                  int* status, cudaStream_t st);

@@ -221,6 +221,11 @@ class SubspaceNufft:
         i = self.info()
         return (i["M1"], i["M2"], i["M3"])
 
+    def launches_per_step(self, B):
+        """Kernel launches of one dc_loss forward + backward on B coils (all K channels):
+        4 forward, 1 residual/loss, one spread per group of 8 channels and 3 inverse passes."""
+        return 4 + 1 + ((self.K + 7) // 8) + 3
+
     @property
     def beta(self):
         return float(lib().sdp_plan_beta(self._h))

@@ -84,7 +84,7 @@ def test_graph_replay_equals_eager_step():
     y_meas = torch.stack([A.forward(_t(synth.ellipsoid_phantom(n, K, seed=7)),
                                     torch.tensor([c], dtype=torch.int32, device="cuda"))[0] for c in range(C)])
     g = graph.DipStepGraph(A, y_meas, _t(x), B=2)
-    assert g.launches_per_step == 9
+    assert g.launches_per_step == A.launches_per_step(2)
     xe = _t(x).requires_grad_(True)
     for cs in ([1, 3], [0, 2], [3, 3]):
         ci = torch.tensor(cs, dtype=torch.int32, device="cuda")
