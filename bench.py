@@ -480,6 +480,33 @@ def run_native(args):
     h2d = xh.numel() * 8 + yh.numel() * 8 + ch.numel() * 4
     d2h = gh.numel() * 8 + 4
 
+    # ---- rows built on the operator: DCF estimation, SVD-MRF initialiser, CG iteration ----
+    from paper_2408_02367_gb300 import recon
+
+    def event_ms(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    Ad = recon.dcf_operator(omega, w.n, w.width, w.oversamp, device=dev)
+    dcf_iters = 10
+    dcf_ms = event_ms(lambda: recon.dcf_pipe_menon(Ad, iters=dcf_iters), 2) / dcf_iters
+    dcf = recon.dcf_pipe_menon(Ad, iters=dcf_iters)
+    dcf = dcf / dcf.mean()
+    del Ad
+    init_ms = event_ms(lambda: recon.svd_mrf_init(A, y_meas, dcf), 2)
+    cg_iters = 3
+    cg_ms = event_ms(lambda: recon.cg_normal(A, y_meas, dcf, iters=cg_iters), 1) / (cg_iters + 1)
+    rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
+            "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
+            "note": "all C coils per CG iteration in minibatches of B; DCF by Pipe-Menon on the interpolator"}
+
     # ---- roofline of the dominant kernel ----
     hbm, peak_kind = peaks()
     sb = stage_bytes(w, B, M, info["ninc"])
@@ -525,6 +552,7 @@ def run_native(args):
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
         "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},
+        "operator_rows": rows,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * B * w.J / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3, "steps": n_e2e},

@@ -169,6 +169,31 @@ int sdp_residual_loss(sdp_plan_t plan, const void* yhat, const void* y_meas, int
                       const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream);
 
 /*
+ * Density-compensated data-consistency loss (Sec. 2, Eq. 2: ||sqrt(DCF) y -
+ * sqrt(DCF) A(x)||^2, per coil Eq. 3), the form sdp_residual_loss takes with
+ * DCF = 1:
+ *   r2[b][j] = 2 dcf[j] (yhat[b][j] - y_meas[meas_idx[b]][j])
+ *   *loss    = sum_b sum_j dcf[j] |yhat[b][j] - y_meas[meas_idx[b]][j]|^2
+ *   dcf      DEVICE float32 [J] per-sample weights (shared by all coils), or
+ *            NULL for 1.  Other arguments as in sdp_residual_loss.
+ */
+int sdp_residual_loss_weighted(sdp_plan_t plan, const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                               const int32_t* meas_idx, int32_t B, const float* dcf, void* r2, float* loss,
+                               void* stream);
+
+/*
+ * Sample-domain Gram of the gridding interpolator with the subspace folded in:
+ *   out[b][j] = sum_k V[t_j,k] sum_m phi(g_j - m) sum_i phi(g_i - m) conj(V[t_i,k]) y[b][i]
+ * i.e. the interpolation step applied to the spread step, without FFT,
+ * deapodisation or coil maps.  With K = 1 and V = 1 it is the
+ * Phi Phi^H of the iterative density compensation of Pipe & Menon 1999,
+ * w <- w / (Phi Phi^H w), which gives the DCF of Eq. 2 (the paper names a DCF
+ * without saying how it is computed).
+ *   y, out  DEVICE complex64 [B][J], 1 <= B <= max_batch; uses the workspace.
+ */
+int sdp_gram_samples(sdp_plan_t plan, const void* y, int32_t B, void* out, void* stream);
+
+/*
  * One application of an operator inside a batch (several volumes / plans):
  *   plan      the item's plan
  *   in        forward: DEVICE x [K][N1][N2][N3]; adjoint: DEVICE y [B][J]

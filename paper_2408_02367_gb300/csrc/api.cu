@@ -641,16 +641,37 @@ int sdp_adjoint_scaled(sdp_plan_t p, const void* y, const int32_t* coil_idx, int
                         static_cast<cudaStream_t>(stream));
 }
 
-int sdp_residual_loss(sdp_plan_t p, const void* yhat, const void* y_meas, int32_t n_meas_rows,
-                      const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream) {
+int sdp_residual_loss_weighted(sdp_plan_t p, const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                               const int32_t* meas_idx, int32_t B, const float* dcf, void* r2, float* loss,
+                               void* stream) {
     if (!p || !yhat || !y_meas || !meas_idx || !r2 || !loss) return SDP_ERR_INVALID_ARG;
     if (B < 1 || B > p->maxB || n_meas_rows < 1) return SDP_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return run(p, ST_LOSS, st, [&] {
         return launch_residual_loss(static_cast<const float2*>(yhat), static_cast<const float2*>(y_meas), meas_idx,
-                                    B, (long long)p->geo.J, n_meas_rows, static_cast<float2*>(r2),
+                                    dcf, B, (long long)p->geo.J, n_meas_rows, static_cast<float2*>(r2),
                                     p->loss_partials, p->loss_counter, loss, p->status, st);
     });
+}
+
+int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* stream) {
+    if (!p || !y || !out || B < 1 || B > p->maxB) return SDP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Geo& g = p->geo;
+    SDP_TRY(run(p, ST_SPREAD, st, [&] {
+        return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->wts, p->V,
+                             static_cast<const float2*>(y), nullptr, B, 0, g.K, p->bufA, p->partials, p->slots_per_b,
+                             p->counters, p->nbins, st);
+    }));
+    return run(p, ST_INTERP, st, [&] {
+        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K, static_cast<float2*>(out), 0,
+                             st);
+    });
+}
+
+int sdp_residual_loss(sdp_plan_t p, const void* yhat, const void* y_meas, int32_t n_meas_rows,
+                      const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream) {
+    return sdp_residual_loss_weighted(p, yhat, y_meas, n_meas_rows, meas_idx, B, nullptr, r2, loss, stream);
 }
 
 int sdp_forward_channels(sdp_plan_t p, const void* x, const int32_t* coil_idx, int32_t B, int32_t k0, int32_t nk,

@@ -1,10 +1,12 @@
-// Data-consistency residual and loss of StoDIP (Sec. 2.1, Eq. 3 with DCF = 1,
-// Algorithm 1 line 5), summed over the coil minibatch:
+// Data-consistency residual and loss of StoDIP (Sec. 2, Eq. 2; Sec. 2.1,
+// Eq. 3; Algorithm 1 line 5), summed over the coil minibatch:
 //
-//   r_b[j] = yhat_b[j] - y_meas[row_b][j],   L = sum_b sum_j |r_b[j]|^2,
+//   r_b[j] = yhat_b[j] - y_meas[row_b][j],   L = sum_b sum_j DCF[j] |r_b[j]|^2,
 //
-// and the gradient of L with respect to yhat in PyTorch's convention,
-// dL/dRe + i dL/dIm = 2 r, which the adjoint consumes in loss.backward().
+// (||sqrt(DCF) y - sqrt(DCF) A x||^2 with a per-sample density compensation,
+// DCF = 1 when none is given) and the gradient of L with respect to yhat in
+// PyTorch's convention, dL/dRe + i dL/dIm = 2 DCF r, which the adjoint
+// consumes in loss.backward().
 //
 // One pass over the residual: a block per 1024 entries of one row, every
 // thread accumulates |r|^2 in float64, blocks reduce in a fixed order and write
@@ -34,7 +36,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // grid = (ceil(J / 1024), B): block (x, b) handles entries [1024 x, 1024 x + 1024) of row b.
 __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
     const float2* yhat, const float2* __restrict__ ymeas, const int* __restrict__ meas_idx,
-    long long J, int nrows, float2* r2, double* __restrict__ partials,
+    const float* __restrict__ dcf, long long J, int nrows, float2* r2, double* __restrict__ partials,
     unsigned int* __restrict__ counter, float* __restrict__ loss, int* status) {
     __shared__ double red[kThreads / 32];
     __shared__ bool s_last;
@@ -59,8 +61,9 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
                 const float2 mv = __ldg(m + j);
                 r = make_float2(hv.x - mv.x, hv.y - mv.y);
             }
-            acc += (double)r.x * r.x + (double)r.y * r.y;
-            o[j] = make_float2(2.f * r.x, 2.f * r.y);
+            const float wd = dcf ? __ldg(dcf + j) : 1.f;
+            acc += (double)wd * ((double)r.x * r.x + (double)r.y * r.y);
+            o[j] = make_float2(2.f * wd * r.x, 2.f * wd * r.y);
         }
     }
     const unsigned nblk = gridDim.x * gridDim.y;
@@ -88,14 +91,14 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
 
 long long residual_loss_partials(int maxB, long long J) { return (long long)maxB * ((J + kPerBlock - 1) / kPerBlock); }
 
-cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
-                                 int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
-                                 int* status, cudaStream_t st) {
+cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, const float* dcf, int B,
+                                 long long J, int nrows, float2* r2, double* partials, unsigned int* counter,
+                                 float* loss, int* status, cudaStream_t st) {
     const long long nx = (J + kPerBlock - 1) / kPerBlock;
     if (nx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nx, (unsigned)B);
-    residual_loss_kernel<<<grid, kThreads, 0, st>>>(yhat, ymeas, meas_idx, J, nrows, r2, partials, counter, loss,
-                                                    status);
+    residual_loss_kernel<<<grid, kThreads, 0, st>>>(yhat, ymeas, meas_idx, dcf, J, nrows, r2, partials, counter,
+                                                    loss, status);
     return cudaGetLastError();
 }
 

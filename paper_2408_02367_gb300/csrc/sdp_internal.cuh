@@ -89,9 +89,9 @@ cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const 
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
                           float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
 long long residual_loss_partials(int maxB, long long J);
-cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, int B, long long J,
-                                 int nrows, float2* r2, double* partials, unsigned int* counter, float* loss,
-                                 int* status, cudaStream_t st);
+cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, const float* dcf, int B,
+                                 long long J, int nrows, float2* r2, double* partials, unsigned int* counter,
+                                 float* loss, int* status, cudaStream_t st);
 
 // Two-pass register FFT kernels (fft2.cu) for the specialised lengths; they
 // return cudaErrorNotSupported for any other length (the Stockham kernels of

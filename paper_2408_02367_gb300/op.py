@@ -80,6 +80,11 @@ EXPORTS = {
                                             ctypes.c_void_p]),
     "sdp_adjoint_scaled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "sdp_residual_loss_weighted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_gram_samples": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "sdp_residual_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
@@ -293,23 +298,44 @@ class SubspaceNufft:
                "sdp_adjoint_scaled")
         return out
 
-    def residual_loss(self, yhat, y_meas, meas_idx, r2=None, loss=None):
-        """r2 = 2 (yhat - y_meas[meas_idx]) and loss = sum |yhat - y_meas[meas_idx]|^2 (device scalar)."""
+    def residual_loss(self, yhat, y_meas, meas_idx, r2=None, loss=None, dcf=None):
+        """r2 = 2 dcf (yhat - y_meas[meas_idx]) and loss = sum dcf |yhat - y_meas[meas_idx]|^2 (device scalar);
+        dcf: float32 [J] device weights or None (1)."""
         B = self._coils(meas_idx)
         _require(yhat, "yhat", torch.complex64, self.device, (B, self.J))
         if y_meas.dim() != 2 or y_meas.shape[1] != self.J:
             raise ValueError("y_meas must be [rows][J]")
         _require(y_meas, "y_meas", torch.complex64, self.device)
+        if dcf is not None:
+            _require(dcf, "dcf", torch.float32, self.device, (self.J,))
         if r2 is None:
             r2 = torch.empty_like(yhat)
         if loss is None:
             loss = torch.empty((), dtype=torch.float32, device=self.device)
         _require(r2, "r2", torch.complex64, self.device, (B, self.J))
         _require(loss, "loss", torch.float32, self.device, ())
-        _check(lib().sdp_residual_loss(self._h, _dev_ptr(yhat), _dev_ptr(y_meas), int(y_meas.shape[0]),
-                                       _dev_ptr(meas_idx), B, _dev_ptr(r2), _dev_ptr(loss),
-                                       _stream_ptr(self.device)), "sdp_residual_loss")
+        st = _stream_ptr(self.device)
+        if dcf is None:
+            rc = lib().sdp_residual_loss(self._h, _dev_ptr(yhat), _dev_ptr(y_meas), int(y_meas.shape[0]),
+                                         _dev_ptr(meas_idx), B, _dev_ptr(r2), _dev_ptr(loss), st)
+        else:
+            rc = lib().sdp_residual_loss_weighted(self._h, _dev_ptr(yhat), _dev_ptr(y_meas), int(y_meas.shape[0]),
+                                                  _dev_ptr(meas_idx), B, _dev_ptr(dcf), _dev_ptr(r2),
+                                                  _dev_ptr(loss), st)
+        _check(rc, "sdp_residual_loss")
         return r2, loss
+
+    def gram_samples(self, y, out=None):
+        """out[b] = Phi_V Phi_V^H y[b]: the spread step followed by the interpolation step."""
+        if y.dim() != 2 or y.shape[1] != self.J or not (1 <= y.shape[0] <= self.max_batch):
+            raise ValueError(f"y must be [B][J] with 1 <= B <= {self.max_batch}")
+        _require(y, "y", torch.complex64, self.device)
+        if out is None:
+            out = torch.empty_like(y)
+        _require(out, "out", torch.complex64, self.device, tuple(y.shape))
+        _check(lib().sdp_gram_samples(self._h, _dev_ptr(y), int(y.shape[0]), _dev_ptr(out),
+                                      _stream_ptr(self.device)), "sdp_gram_samples")
+        return out
 
     # -- profiling --
     def profile(self, enable=True):
@@ -393,9 +419,9 @@ class _DataConsistency(torch.autograd.Function):
     the library's kernels."""
 
     @staticmethod
-    def forward(ctx, x, coil_idx, meas_idx, y_meas, op):
+    def forward(ctx, x, coil_idx, meas_idx, y_meas, op, dcf):
         yhat = op.forward(x.contiguous(), coil_idx)
-        r2, loss = op.residual_loss(yhat, y_meas, meas_idx, r2=yhat)   # r2 overwrites yhat in place
+        r2, loss = op.residual_loss(yhat, y_meas, meas_idx, r2=yhat, dcf=dcf)   # r2 overwrites yhat in place
         ctx.op = op
         ctx.save_for_backward(coil_idx, r2)
         return loss
@@ -406,16 +432,17 @@ class _DataConsistency(torch.autograd.Function):
         gx = None
         if ctx.needs_input_grad[0]:
             gx = ctx.op.adjoint_scaled(r2, coil_idx, gL.to(torch.float32).contiguous())
-        return gx, None, None, None, None
+        return gx, None, None, None, None, None
 
 
-def dc_loss(op: SubspaceNufft, x, coil_idx, y_meas, meas_idx=None):
-    """Differentiable data-consistency loss of a coil minibatch (Algorithm 1, lines 4-5).
+def dc_loss(op: SubspaceNufft, x, coil_idx, y_meas, meas_idx=None, dcf=None):
+    """Differentiable data-consistency loss of a coil minibatch (Algorithm 1, lines 4-5; Eq. 2/3).
 
     y_meas [rows][J]: measured k-space; row meas_idx[b] is compared with coil
     coil_idx[b] (default meas_idx = coil_idx, i.e. y_meas holds all C coils).
+    dcf: optional float32 [J] density compensation (Eq. 2), None for DCF = 1.
     """
-    return _DataConsistency.apply(x, coil_idx, coil_idx if meas_idx is None else meas_idx, y_meas, op)
+    return _DataConsistency.apply(x, coil_idx, coil_idx if meas_idx is None else meas_idx, y_meas, op, dcf)
 
 
 def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda"):
