@@ -503,7 +503,14 @@ def run_native(args):
     init_ms = event_ms(lambda: recon.svd_mrf_init(A, y_meas, dcf), 2)
     cg_iters = 3
     cg_ms = event_ms(lambda: recon.cg_normal(A, y_meas, dcf, iters=cg_iters), 1) / (cg_iters + 1)
+    xtv = x.detach()
+    tv_grad_buf = torch.empty_like(xtv)
+    tv_val_ms = event_ms(lambda: A.tv_value(xtv, 1e-7, 1e-6), 10)
+    tv_grad_ms = event_ms(lambda: A.tv_grad(xtv, 1e-7, 1e-6, out=tv_grad_buf), 10)
+    xb = 8.0 * xtv.numel()
     rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
+            "tv_value_ms": tv_val_ms, "tv_value_gbs": xb / (tv_val_ms * 1e-3) / 1e9,
+            "tv_grad_ms": tv_grad_ms, "tv_grad_gbs": 2 * xb / (tv_grad_ms * 1e-3) / 1e9,
             "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
             "note": "all C coils per CG iteration in minibatches of B; DCF by Pipe-Menon on the interpolator"}
 

@@ -194,6 +194,22 @@ int sdp_residual_loss_weighted(sdp_plan_t plan, const void* yhat, const void* y_
 int sdp_gram_samples(sdp_plan_t plan, const void* y, int32_t B, void* out, void* stream);
 
 /*
+ * Spatial total variation of the TSMI, the penalty of Algorithm 1 line 6
+ * (loss = L_c + lambda TV(x_hat), Sec. 2.1).  The paper does not define TV;
+ * this is the isotropic TV of every subspace channel with smoothing eps > 0,
+ * forward differences D_d and a zero difference at the last index of an axis:
+ *   TV(x) = sum_k sum_n sqrt(|D1 x_k(n)|^2 + |D2 x_k(n)|^2 + |D3 x_k(n)|^2 + eps^2)
+ *   x      DEVICE complex64 [K][N1][N2][N3] (the plan's image size)
+ *   value  DEVICE float32 scalar: lambda TV(x), accumulated in float64, fixed order
+ *   out    DEVICE complex64 [K][N1][N2][N3]:
+ *          (accumulate ? out : 0) + lambda (*scale) (dTV/dRe + i dTV/dIm)
+ *   scale  DEVICE float32 scalar or NULL (1); out must not alias x.
+ */
+int sdp_tv_value(sdp_plan_t plan, const void* x, float eps, float lambda, float* value, void* stream);
+int sdp_tv_grad(sdp_plan_t plan, const void* x, float eps, float lambda, const float* scale, void* out,
+                int32_t accumulate, void* stream);
+
+/*
  * One application of an operator inside a batch (several volumes / plans):
  *   plan      the item's plan
  *   in        forward: DEVICE x [K][N1][N2][N3]; adjoint: DEVICE y [B][J]
@@ -283,7 +299,7 @@ int64_t sdp_launch_count(void);
  * writes up to `cap` stages: ms[s] = summed milliseconds, launches[s] = count.
  * Stages: 0 prologue+FFT axis 3, 1 FFT axis 2, 2 FFT axis 1, 3 interpolation,
  * 4 spread, 5 inverse FFT axis 1, 6 inverse FFT axis 2, 7 inverse FFT axis 3
- * + epilogue, 8 residual and loss.  Reading resets the sums.  Returns the number of stages written
+ * + epilogue, 8 residual and loss, 9 total variation.  Reading resets the sums.  Returns the number of stages written
  * or a negative status.  Profiling is off by default and costs two event
  * records per launch when on.
  */

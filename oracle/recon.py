@@ -87,3 +87,45 @@ def cg_normal(geo: O.Geometry, y_all, S, V, omega, frame, dcf=None, iters: int =
         rs = rs_new
         hist.append(float(np.sqrt(rs)))
     return x, hist
+
+
+# ----------------------------------------------------------------------------
+# Spatial total variation, Algorithm 1 line 6 (reading: isotropic, eps-smoothed,
+# per channel, forward differences with a zero difference at the last index)
+# ----------------------------------------------------------------------------
+
+def _forward_diffs(x):
+    """D_d x for d = 1, 2, 3 over the last three axes of x [K][N1][N2][N3]."""
+    out = []
+    for ax in (1, 2, 3):
+        d = np.zeros_like(x)
+        sl_hi = [slice(None)] * 4
+        sl_lo = [slice(None)] * 4
+        sl_hi[ax] = slice(1, None)
+        sl_lo[ax] = slice(0, -1)
+        d[tuple(sl_lo)] = x[tuple(sl_hi)] - x[tuple(sl_lo)]
+        out.append(d)
+    return out
+
+
+def tv_value(x, eps):
+    """sum_k sum_n sqrt(|D1 x|^2 + |D2 x|^2 + |D3 x|^2 + eps^2)."""
+    x = np.asarray(x, np.complex128)
+    d1, d2, d3 = _forward_diffs(x)
+    return float(np.sum(np.sqrt(np.abs(d1) ** 2 + np.abs(d2) ** 2 + np.abs(d3) ** 2 + eps ** 2)))
+
+
+def tv_grad(x, eps):
+    """dTV/dRe + i dTV/dIm = sum_d [ D_d x(m - e_d) / s(m - e_d) - D_d x(m) / s(m) ]."""
+    x = np.asarray(x, np.complex128)
+    ds = _forward_diffs(x)
+    s = np.sqrt(sum(np.abs(d) ** 2 for d in ds) + eps ** 2)
+    g = -sum(ds) / s
+    for ax, d in zip((1, 2, 3), ds):
+        q = d / s
+        sl_dst = [slice(None)] * 4
+        sl_src = [slice(None)] * 4
+        sl_dst[ax] = slice(1, None)
+        sl_src[ax] = slice(0, -1)
+        g[tuple(sl_dst)] += q[tuple(sl_src)]
+    return g

@@ -59,6 +59,8 @@ struct sdp_plan_s {
     int* status = nullptr;
     double* loss_partials = nullptr;
     unsigned int* loss_counter = nullptr;
+    double* tv_part = nullptr;
+    unsigned int* tv_counter = nullptr;
     float2* bufA = nullptr;
     float2* bufB = nullptr;
     size_t workspace_bytes = 0;
@@ -367,6 +369,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_TRY(dev_alloc(p, &p->status, 1));
     SDP_TRY(dev_alloc(p, &p->loss_partials, (size_t)residual_loss_partials(p->maxB, J)));
     SDP_TRY(dev_alloc(p, &p->loss_counter, 1));
+    SDP_TRY(dev_alloc(p, &p->tv_part, (size_t)tv_partials(K, nvox)));
+    SDP_TRY(dev_alloc(p, &p->tv_counter, 1));
     const size_t before = p->total_bytes;
     const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);
     const size_t gridB = (size_t)(p->n[0] * p->M[1] * p->M[2]);
@@ -385,6 +389,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * ((K + 7) / 8) * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
+    SDP_CUDA(cudaMemsetAsync(p->tv_counter, 0, sizeof(unsigned int), st));
     SDP_CUDA(launch_kb_weights(g, p->pts, p->wts, st));
     SDP_CUDA(cudaStreamSynchronize(st));
     size_t o = 0;
@@ -651,6 +656,26 @@ int sdp_residual_loss_weighted(sdp_plan_t p, const void* yhat, const void* y_mea
         return launch_residual_loss(static_cast<const float2*>(yhat), static_cast<const float2*>(y_meas), meas_idx,
                                     dcf, B, (long long)p->geo.J, n_meas_rows, static_cast<float2*>(r2),
                                     p->loss_partials, p->loss_counter, loss, p->status, st);
+    });
+}
+
+int sdp_tv_value(sdp_plan_t p, const void* x, float eps, float lambda, float* value, void* stream) {
+    if (!p || !x || !value || !(eps > 0.f)) return SDP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return run(p, ST_TV, st, [&] {
+        return launch_tv_value(p->geo, static_cast<const float2*>(x), eps, lambda, p->tv_part, p->tv_counter, value,
+                               st);
+    });
+}
+
+int sdp_tv_grad(sdp_plan_t p, const void* x, float eps, float lambda, const float* scale, void* out,
+                int32_t accumulate, void* stream) {
+    if (!p || !x || !out || !(eps > 0.f)) return SDP_ERR_INVALID_ARG;
+    if (x == out) return SDP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return run(p, ST_TV, st, [&] {
+        return launch_tv_grad(p->geo, static_cast<const float2*>(x), eps, lambda, scale, static_cast<float2*>(out),
+                              accumulate ? 1 : 0, st);
     });
 }
 

@@ -15,7 +15,7 @@ constexpr int kMaxRadixStages = 12;
 constexpr int kMaxWidth = 8;
 constexpr int kMaxK = 16;
 constexpr int kMaxBatch = 64;
-constexpr int kNumStages = 9;   // profiling stages, see stodip_op.h
+constexpr int kNumStages = 10;  // profiling stages, see stodip_op.h
 
 enum Stage {
     ST_FWD_FFT3 = 0,
@@ -27,6 +27,7 @@ enum Stage {
     ST_ADJ_FFT2 = 6,
     ST_ADJ_FFT3 = 7,
     ST_LOSS = 8,
+    ST_TV = 9,
 };
 
 // One axis of the 3D FFT: length L = prod(radix[0..nst)), twiddles
@@ -108,6 +109,13 @@ cudaError_t launch_fft2_adj_epilogue(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int accumulate,
                                      int* status, cudaStream_t st);
+
+// Total variation of the image (tv.cu).
+long long tv_partials(int K, long long nvox);
+cudaError_t launch_tv_value(const Geo& g, const float2* x, float eps, float lambda, double* partials,
+                            unsigned int* counter, float* out, cudaStream_t st);
+cudaError_t launch_tv_grad(const Geo& g, const float2* x, float eps, float lambda, const float* scale, float2* out,
+                           int accumulate, cudaStream_t st);
 
 // Host helpers.
 bool fft_factor(int L, FftAxis* ax);

@@ -25,7 +25,7 @@ SDP_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
                 5: "bounds", 6: "unsupported"}
 STAGES = ["fwd_prologue_fft3", "fwd_fft2", "fwd_fft1", "interp", "spread", "adj_ifft1", "adj_ifft2",
-          "adj_ifft3_epilogue", "residual_loss"]
+          "adj_ifft3_epilogue", "residual_loss", "tv"]
 
 
 class SdpError(RuntimeError):
@@ -83,6 +83,10 @@ EXPORTS = {
     "sdp_residual_loss_weighted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_tv_value": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_tv_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "sdp_gram_samples": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "sdp_residual_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
@@ -337,6 +341,28 @@ class SubspaceNufft:
                                       _stream_ptr(self.device)), "sdp_gram_samples")
         return out
 
+    def tv_value(self, x, lam=1.0, eps=1e-6, out=None):
+        """lam TV(x) as a device float32 scalar (isotropic, eps-smoothed, per channel)."""
+        _require(x, "x", torch.complex64, self.device, (self.K,) + self.n)
+        if out is None:
+            out = torch.empty((), dtype=torch.float32, device=self.device)
+        _check(lib().sdp_tv_value(self._h, _dev_ptr(x), float(eps), float(lam), _dev_ptr(out),
+                                  _stream_ptr(self.device)), "sdp_tv_value")
+        return out
+
+    def tv_grad(self, x, lam=1.0, eps=1e-6, scale=None, out=None, accumulate=False):
+        """(accumulate ? out : 0) + lam (*scale) grad TV(x)."""
+        _require(x, "x", torch.complex64, self.device, (self.K,) + self.n)
+        if out is None:
+            out = torch.empty_like(x)
+        _require(out, "out", torch.complex64, self.device, (self.K,) + self.n)
+        if scale is not None:
+            _require(scale, "scale", torch.float32, self.device, ())
+        _check(lib().sdp_tv_grad(self._h, _dev_ptr(x), float(eps), float(lam),
+                                 _dev_ptr(scale) if scale is not None else None, _dev_ptr(out),
+                                 int(bool(accumulate)), _stream_ptr(self.device)), "sdp_tv_grad")
+        return out
+
     # -- profiling --
     def profile(self, enable=True):
         _check(lib().sdp_profile_enable(self._h, int(bool(enable))), "sdp_profile_enable")
@@ -443,6 +469,28 @@ def dc_loss(op: SubspaceNufft, x, coil_idx, y_meas, meas_idx=None, dcf=None):
     dcf: optional float32 [J] density compensation (Eq. 2), None for DCF = 1.
     """
     return _DataConsistency.apply(x, coil_idx, coil_idx if meas_idx is None else meas_idx, y_meas, op, dcf)
+
+
+class _TotalVariation(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, op, lam, eps):
+        xc = x.contiguous()
+        ctx.op, ctx.lam, ctx.eps = op, lam, eps
+        ctx.save_for_backward(xc)
+        return op.tv_value(xc, lam, eps)
+
+    @staticmethod
+    def backward(ctx, gL):
+        (x,) = ctx.saved_tensors
+        gx = None
+        if ctx.needs_input_grad[0]:
+            gx = ctx.op.tv_grad(x, ctx.lam, ctx.eps, scale=gL.to(torch.float32).contiguous())
+        return gx, None, None, None
+
+
+def tv_loss(op: SubspaceNufft, x, lam: float, eps: float = 1e-6):
+    """Differentiable lam TV(x) (Algorithm 1 line 6), value and gradient in the library's kernels."""
+    return _TotalVariation.apply(x, op, float(lam), float(eps))
 
 
 def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda"):

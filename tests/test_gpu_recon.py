@@ -93,3 +93,25 @@ def test_cg_on_the_normal_equations(case):
         print(f"CG lam={lam}: rel {e:.2e}, residuals {hg[-1] / hg[0]:.3e} vs {hr[-1] / hr[0]:.3e}")
         assert e < 1e-4
         assert abs(hg[-1] / hg[0] - hr[-1] / hr[0]) < 1e-3 * max(1e-3, hr[-1] / hr[0]) + 1e-6
+
+
+def test_total_variation_value_gradient_and_autograd(case):
+    from paper_2408_02367_gb300 import op
+    A = case["A"]
+    eps, lam = 1e-2, 0.3
+    x = case["x"]
+    v = A.tv_value(_t(x), lam, eps).item()
+    v_ref = lam * R.tv_value(x, eps)
+    assert abs(v - v_ref) / v_ref < 1e-5
+    g = A.tv_grad(_t(x), lam, eps).cpu().numpy()
+    assert rel(g, lam * R.tv_grad(x, eps)) < FP32_BOUND
+    # loss = data consistency + lam TV, one backward through both (Algorithm 1 lines 4-7)
+    coils = np.array([0, 2], np.int32)
+    xg = _t(x).requires_grad_(True)
+    loss = op.dc_loss(A, xg, _t(coils), _t(case["y_all"].astype(np.complex64))) + op.tv_loss(A, xg, lam, eps)
+    loss.backward()
+    fwd = lambda u: O.gridding_forward(case["geo"], u, case["S"], case["V"], case["om"], case["fr"], coils)
+    adj = lambda r: O.gridding_adjoint(case["geo"], r, case["S"], case["V"], case["om"], case["fr"], coils)
+    ym = case["y_all"][coils]
+    g_ref = O.dip_grad(fwd, adj, x.astype(np.complex128), ym) + lam * R.tv_grad(x, eps)
+    assert rel(xg.grad.cpu().numpy(), g_ref) < FP32_BOUND

@@ -90,3 +90,27 @@ def test_cg_reaches_the_least_squares_solution_of_a_small_system():
     xls = np.linalg.lstsq(A, y.ravel() * np.sqrt(np.tile(dcf, 2)), rcond=None)[0]
     assert P.rel(xcg.ravel(), xls) < 1e-6
     assert hist[-1] < 1e-6 * hist[0]
+
+
+def test_tv_closed_forms_constant_and_ramp():
+    K, n = 2, (5, 4, 6)
+    eps = 1e-3
+    c = np.full((K,) + n, 0.7 - 0.2j)
+    assert abs(R.tv_value(c, eps) - K * np.prod(n) * eps) < 1e-12
+    assert np.max(np.abs(R.tv_grad(c, eps))) == 0.0
+    a = 0.3 + 0.4j                                   # |a| = 0.5, ramp along axis 1
+    ramp = np.broadcast_to(a * np.arange(n[0])[None, :, None, None], (K,) + n)
+    expect = K * n[1] * n[2] * ((n[0] - 1) * np.sqrt(0.25 + eps ** 2) + eps)
+    assert abs(R.tv_value(ramp, eps) - expect) < 1e-10
+
+
+def test_tv_gradient_matches_central_differences():
+    x = synth.random_complex((2, 6, 5, 7), 111).astype(np.complex128)
+    eps = 0.05
+    g = R.tv_grad(x, eps)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        d = rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)
+        h = 1e-6
+        fd = (R.tv_value(x + h * d, eps) - R.tv_value(x - h * d, eps)) / (2 * h)
+        assert abs(fd - np.real(np.vdot(g, d))) / abs(fd) < 1e-6
