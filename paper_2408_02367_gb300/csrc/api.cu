@@ -369,7 +369,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_TRY(dev_alloc(p, &p->status, 1));
     SDP_TRY(dev_alloc(p, &p->loss_partials, (size_t)residual_loss_partials(p->maxB, J)));
     SDP_TRY(dev_alloc(p, &p->loss_counter, 1));
-    SDP_TRY(dev_alloc(p, &p->tv_part, (size_t)tv_partials(K, nvox)));
+    SDP_TRY(dev_alloc(p, &p->tv_part, (size_t)tv_partials(K, (int)p->n[0], (int)p->n[1], (int)p->n[2])));
     SDP_TRY(dev_alloc(p, &p->tv_counter, 1));
     const size_t before = p->total_bytes;
     const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);

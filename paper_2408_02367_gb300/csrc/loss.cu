@@ -8,11 +8,12 @@
 // PyTorch's convention, dL/dRe + i dL/dIm = 2 DCF r, which the adjoint
 // consumes in loss.backward().
 //
-// One pass over the residual: a block per 1024 entries of one row, every
-// thread accumulates |r|^2 in float64, blocks reduce in a fixed order and write
-// one partial each; the last block to finish (device-scope counter, no
-// waiting) sums the partials in a fixed order, so the loss is bitwise
-// repeatable.
+// One pass over the residual: a block per 1024 entries of one row.  A thread
+// sums its 4 entries and a warp its 128 in float32 (the FP64 pipe of this part
+// is far too narrow for per-entry float64 work), the 8 warps of a block are
+// added in float64 in a fixed order into one partial per block, and the last
+// block to finish (device-scope counter, no waiting) sums the partials in
+// float64 in a fixed order, so the loss is bitwise repeatable.
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -22,7 +23,18 @@ constexpr int kThreads = 256;
 constexpr int kPerThread = 4;                       // residual entries per thread
 constexpr int kPerBlock = kThreads * kPerThread;    // one block covers 1024 entries of one row
 
-// Fixed-order block reduction of a double (warp butterflies, then warps in order).
+// Fixed-order block reduction: float32 warp butterflies, then the warps in order in float64.
+__device__ __forceinline__ double block_sum_f(float v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    return s;   // valid in thread 0
+}
+
+// The same in float64 throughout, for the few block partials.
 __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -48,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
     const float2* m = ymeas + (long long)(ok ? row : 0) * J;
     float2* o = r2 + (long long)b * J;
     const long long j0 = (long long)blockIdx.x * kPerBlock;
-    double acc = 0.0;
+    float acc = 0.f;
     // consecutive threads take consecutive entries: each pass of the block is one
     // coalesced 2 KB read of yhat and of y_meas
 #pragma unroll
@@ -62,13 +74,13 @@ __global__ void __launch_bounds__(kThreads) residual_loss_kernel(
                 r = make_float2(hv.x - mv.x, hv.y - mv.y);
             }
             const float wd = dcf ? __ldg(dcf + j) : 1.f;
-            acc += (double)wd * ((double)r.x * r.x + (double)r.y * r.y);
+            acc = fmaf(wd, fmaf(r.x, r.x, r.y * r.y), acc);
             o[j] = make_float2(2.f * wd * r.x, 2.f * wd * r.y);
         }
     }
     const unsigned nblk = gridDim.x * gridDim.y;
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-    const double bs = block_sum(acc, red);
+    const double bs = block_sum_f(acc, red);
     if (threadIdx.x == 0) {
         partials[bid] = bs;
         __threadfence();

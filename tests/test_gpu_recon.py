@@ -115,3 +115,20 @@ def test_total_variation_value_gradient_and_autograd(case):
     ym = case["y_all"][coils]
     g_ref = O.dip_grad(fwd, adj, x.astype(np.complex128), ym) + lam * R.tv_grad(x, eps)
     assert rel(xg.grad.cpu().numpy(), g_ref) < FP32_BOUND
+
+
+def test_total_variation_ragged_tiles_and_accumulate():
+    """A volume that spans several 32 x 8 tiles and 16-plane segments with ragged edges on every axis."""
+    from paper_2408_02367_gb300 import op
+    n, K = (35, 19, 41), 2
+    x = synth.random_complex((K,) + n, 121)
+    om, fr = synth.spiral_trajectory(4, 1, 64)
+    A = op.make_operator(om, fr, n, 4, 1.25, synth.subspace_basis(4, K), synth.coil_maps(n, 1), max_batch=1)
+    eps, lam = 0.05, 0.9
+    v = A.tv_value(_t(x), lam, eps).item()
+    v_ref = lam * R.tv_value(x, eps)
+    assert abs(v - v_ref) / v_ref < 1e-5
+    base = synth.random_complex((K,) + n, 122)
+    out = _t(base)
+    A.tv_grad(_t(x), lam, eps, out=out, accumulate=True)
+    assert rel(out.cpu().numpy(), base + lam * R.tv_grad(x, eps)) < FP32_BOUND
