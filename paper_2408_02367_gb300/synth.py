@@ -222,3 +222,62 @@ def make_problem(w: Workload, seed: int = SEED_PHANTOM):
     V = subspace_basis(w.T, w.K)
     omega, frame = spiral_trajectory(w.T, w.arms, w.arm_len)
     return x, S, V, omega, frame
+
+
+# ----------------------------------------------------------------------------
+# Synthetic MRF dictionaries for dictionary matching (no Bloch simulation)
+# ----------------------------------------------------------------------------
+
+SEED_DM = 6
+
+
+def mrf_dictionary(T: int, n_t1: int = 64, n_t2: int = 48, dtype=np.complex64):
+    """A smooth parametric stand-in for a Bloch-simulated MRF dictionary.
+
+    Fingerprints f_t(T1, T2) = sin(a_t) (1 - 2 exp(-tau_t / T1)) exp(-kappa_t / T2) exp(i phi_t)
+    for t = 0..T-1: an inversion-recovery-like T1 weighting, a T2 weighting
+    that varies along the train, a smooth flip-angle train a_t and a slow
+    phase phi_t.  It is not a Bloch response; it has what matching needs:
+    atoms that vary smoothly with (T1, T2), so that neighbours are highly
+    correlated, and norms that differ from atom to atom.  T1 on a log grid
+    100..4000 ms, T2 on a log grid 10..2000 ms, pairs with T2 < T1 only.
+
+    Returns (fingerprints [P][T], params [P][2] float32 (T1, T2) in ms).
+    """
+    t = np.arange(T, dtype=np.float64)
+    tr = 10.0
+    a = np.deg2rad(5.0 + 55.0 * np.sin(np.pi * t / 200.0) ** 2)
+    tau = (t + 1.0) * tr
+    kappa = 2.0 + 60.0 * np.sin(3.0 * np.pi * t / T) ** 2
+    phi = 0.3 * np.sin(2.0 * np.pi * t / T)
+    t1 = np.geomspace(100.0, 4000.0, n_t1)
+    t2 = np.geomspace(10.0, 2000.0, n_t2)
+    pairs = np.array([(a1, a2) for a1 in t1 for a2 in t2 if a2 < a1])
+    f = (np.sin(a)[None, :] * (1.0 - 2.0 * np.exp(-tau[None, :] / pairs[:, :1]))
+         * np.exp(-kappa[None, :] / pairs[:, 1:]) * np.exp(1j * phi)[None, :])
+    return f.astype(dtype), pairs.astype(np.float32)
+
+
+def compress_dictionary(fingerprints, K: int):
+    """Temporal SVD compression (Sec. 2 after Eq. 1): V = the first K right singular
+    vectors of the dictionary, atoms d_p = V^H f_p.  Returns (D [P][K], V [T][K])."""
+    f = np.asarray(fingerprints, np.complex128)
+    _, _, wh = np.linalg.svd(f, full_matrices=False)
+    V = wh[:K].conj().T
+    D = f @ V.conj()
+    return D.astype(np.complex64), V.astype(np.complex64)
+
+
+def dm_volume(D, nvox: int, noise: float = 0.0, seed: int = SEED_DM, dtype=np.complex64):
+    """A TSMI [K][nvox] whose voxels are PD_v d_{p_v} plus complex noise (std
+    `noise` times the mean voxel norm), with p_v uniform over the atoms and
+    PD_v complex with magnitude in [0.5, 2].  Returns (x, p, PD)."""
+    D = np.asarray(D, np.complex128)
+    rng = np.random.default_rng(seed)
+    p = rng.integers(0, D.shape[0], size=nvox)
+    pd = rng.uniform(0.5, 2.0, size=nvox) * np.exp(1j * rng.uniform(-np.pi, np.pi, size=nvox))
+    x = (pd[:, None] * D[p]).T
+    if noise > 0:
+        s = noise * np.mean(np.linalg.norm(x, axis=0)) / math.sqrt(2.0 * D.shape[1])
+        x = x + s * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape))
+    return x.astype(dtype), p.astype(np.int64), pd
