@@ -523,12 +523,52 @@ def run_native(args):
     tv_val_ms = kernel_ms(lambda: A.tv_value(xtv, 1e-7, 1e-6, out=tv_val_buf), 20)
     tv_grad_ms = kernel_ms(lambda: A.tv_grad(xtv, 1e-7, 1e-6, out=tv_grad_buf), 20)
     xb = 8.0 * xtv.numel()
+
+    # dictionary matching of the whole TSMI volume against a synthetic MRF dictionary
+    from paper_2408_02367_gb300 import dm as dm_mod
+    fp, params = synth.mrf_dictionary(480, 128, 96)
+    Dm, _ = synth.compress_dictionary(fp, w.K)
+    xd_np, _, _ = synth.dm_volume(Dm, w.nvox, noise=0.01, seed=7)
+    xd = torch.from_numpy(xd_np.reshape((w.K,) + tuple(w.n))).to(dev)
+    del xd_np
+    matcher = dm_mod.DictionaryMatcher(torch.from_numpy(Dm).to(dev), max_vox=w.nvox,
+                                       params=torch.from_numpy(params).to(dev))
+    dm_out = (torch.empty(tuple(w.n), dtype=torch.int32, device=dev),
+              torch.empty(tuple(w.n), dtype=torch.complex64, device=dev),
+              torch.empty(tuple(w.n) + (2,), dtype=torch.float32, device=dev))
+
+    def dm_call():
+        matcher.match(xd, out=dm_out, qmap=True)
+
+    dm_call()
+    torch.cuda.synchronize()
+    dm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for i, (a_ev, b_ev) in enumerate(dm_ev):
+        flush.fill_(float(i))
+        a_ev.record()
+        dm_call()
+        b_ev.record()
+    torch.cuda.synchronize()
+    dm_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in dm_ev)[len(dm_ev) // 2]
+    dm_info = matcher.info()
+    dm_status = matcher.status()
+    dm_tflops = dm_info["flops_per_voxel"] * w.nvox / (dm_ms * 1e-3) / 1e12
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
+    del matcher, xd, dm_out
+
     rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
             "tv_value_ms": tv_val_ms, "tv_value_gbs": xb / (tv_val_ms * 1e-3) / 1e9,
             "tv_grad_ms": tv_grad_ms, "tv_grad_gbs": 2 * xb / (tv_grad_ms * 1e-3) / 1e9,
             "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
+            "dm_ms": dm_ms, "dm_atoms": int(Dm.shape[0]), "dm_voxels": int(w.nvox),
+            "dm_gpairs_per_s": w.nvox * Dm.shape[0] / (dm_ms * 1e-3) / 1e9,
+            "dm_tensor_tflops": dm_tflops, "dm_tensor_frac_of_measured_bf16": dm_tflops / bf16_peak,
+            "dm_status": dm_status,
             "note": "all C coils per CG iteration in minibatches of B; DCF by Pipe-Menon on the interpolator; "
-                    "TV kernels timed alone by the library's stage events, L2 flushed before each call"}
+                    "TV kernels timed alone by the library's stage events, L2 flushed before each call; "
+                    "dictionary matching: one match of all voxels (prep + tcgen05 score GEMM + refine), "
+                    "median of 5, L2 flushed before each, fp16 tensor flops counted with padding to K=16"}
 
     # ---- roofline of the dominant kernel ----
     hbm, peak_kind = peaks()

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstodip_op.so")
-SOURCES = ["api.cu", "fft.cu", "fft2.cu", "interp.cu", "spread.cu", "loss.cu", "noalloc.cu", "tv.cu"]
+SOURCES = ["api.cu", "fft.cu", "fft2.cu", "interp.cu", "spread.cu", "loss.cu", "noalloc.cu", "tv.cu", "dm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,8 +46,9 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "stodip_op.h"),
-                                                               os.path.abspath(__file__)]
+    inc = os.path.join(ROOT, "include")
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
+            + [os.path.abspath(__file__)])
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

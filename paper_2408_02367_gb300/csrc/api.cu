@@ -29,6 +29,8 @@ struct ProfRec {
 
 }  // namespace
 
+void sdp::note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 struct sdp_plan_s {
     int dev = 0;
     Geo geo{};

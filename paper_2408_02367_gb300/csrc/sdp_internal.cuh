@@ -112,6 +112,9 @@ cudaError_t launch_fft2_adj_epilogue(const Geo& g, const FftAxis& ax, const floa
 
 // Total variation of the image (tv.cu).
 long long tv_partials(int K, int N1, int N2, int N3);
+
+// Count kernel launches made outside the plan's run() wrapper (sdp_launch_count).
+void note_launches(long long n);
 cudaError_t launch_tv_value(const Geo& g, const float2* x, float eps, float lambda, double* partials,
                             unsigned int* counter, float* out, cudaStream_t st);
 cudaError_t launch_tv_grad(const Geo& g, const float2* x, float eps, float lambda, const float* scale, float2* out,

@@ -108,6 +108,14 @@ EXPORTS = {
     "sdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sdp_grid_size": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_double, ctypes.c_int32]),
     "sdp_kb_beta": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double]),
+    # dictionary matching (include/stodip_dm.h)
+    "sdp_dm_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
+    "sdp_dm_destroy": (None, [ctypes.c_void_p]),
+    "sdp_dm_match": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_dm_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_dm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
 }
 
 

@@ -280,4 +280,4 @@ def dm_volume(D, nvox: int, noise: float = 0.0, seed: int = SEED_DM, dtype=np.co
     if noise > 0:
         s = noise * np.mean(np.linalg.norm(x, axis=0)) / math.sqrt(2.0 * D.shape[1])
         x = x + s * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape))
-    return x.astype(dtype), p.astype(np.int64), pd
+    return np.ascontiguousarray(x.astype(dtype)), p.astype(np.int64), pd

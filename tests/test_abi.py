@@ -1,5 +1,5 @@
 """The C ABI library builds, loads without a GPU and exports every entry point
-that include/stodip_op.h declares; host-only entry points answer correctly."""
+that include/*.h declares; host-only entry points answer correctly."""
 import ctypes
 import os
 import re
@@ -9,7 +9,8 @@ import pytest
 from oracle import nufft as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "stodip_op.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +21,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(sdp_[a-z0-9_]+)\s*\(", text)))
 
@@ -29,7 +30,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for need in ["sdp_plan_create", "sdp_plan_destroy", "sdp_forward", "sdp_adjoint", "sdp_forward_batched",
                  "sdp_adjoint_batched", "sdp_status", "sdp_workspace_bytes", "sdp_strerror",
-                 "sdp_residual_loss", "sdp_adjoint_scaled"]:
+                 "sdp_residual_loss", "sdp_adjoint_scaled", "sdp_dm_create", "sdp_dm_match", "sdp_dm_destroy"]:
         assert need in names
 
 
@@ -73,3 +74,17 @@ def test_grid_size_rejects_out_of_range(lib):
     assert lib.sdp_grid_size(10, 0.5, 4) == -1
     assert lib.sdp_grid_size(10, 2.0, 9) == -1
     assert lib.sdp_kb_beta(2, 1.0) > 0 or lib.sdp_kb_beta(2, 1.0) == -1.0
+
+
+def test_dictionary_matcher_rejects_bad_arguments_on_the_host(lib):
+    h = ctypes.c_void_p(1234)
+    assert lib.sdp_dm_create(None, None, None, 1, 1, 1, None) == 1
+    assert lib.sdp_dm_create(ctypes.byref(h), None, None, 10, 5, 100, None) == 1
+    assert h.value is None
+    assert lib.sdp_dm_create(ctypes.byref(h), ctypes.c_void_p(16), None, 10, 17, 100, None) == 1   # K > 16
+    assert lib.sdp_dm_create(ctypes.byref(h), ctypes.c_void_p(16), None, 0, 5, 100, None) == 1     # P < 1
+    assert lib.sdp_dm_match(None, None, 0, None, None, None, None) == 1
+    assert lib.sdp_dm_status(None, None) == 1
+    buf = (ctypes.c_int64 * 8)()
+    assert lib.sdp_dm_info(None, buf, 8) == 1
+    lib.sdp_dm_destroy(None)

@@ -1,0 +1,140 @@
+"""Dictionary matching on the GPU (tcgen05 score GEMM + float32 refine) against
+the FP64 oracle on the same seeded inputs.
+
+The GPU picks the 32-atom chunk from scores of fp16-rounded unit vectors and the
+atom inside the chunk in float32.  For unit vectors a, b of R^{2K} rounded to
+fp16 (unit roundoff u = 2^-11) the real and imaginary parts of d^H x each move
+by at most 2u, so |d^H x| by at most 2 sqrt(2) u and |d^H x|^2 (<= 1) by at most
+4 sqrt(2) u + 8 u^2 < 2.8e-3; two atoms compared across chunks can therefore be
+swapped only when their normalised scores squared are within 2 x 2.8e-3 of each
+other.  Hence:
+  * every voxel's matched atom scores within SCORE_TOL of the best one (valid);
+  * where the best atom leads every atom outside its chunk by more than
+    SCORE_TOL and every other atom of its chunk by more than FP32_GAP, the
+    index is the oracle's exactly (unique);
+  * PD of the matched atom matches its least-squares coefficient in FP64.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dm as DM
+from paper_2408_02367_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SCORE_TOL = 5.6e-3      # 2 x 2.8e-3, on |d^H x|^2 / (||d||^2 ||x||^2)
+FP32_GAP = 1e-5
+PD_RTOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2408_02367_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def random_atoms(P, K, seed):
+    rng = np.random.default_rng(seed)
+    scale = rng.uniform(0.3, 3.0, size=(P, 1))
+    return ((rng.standard_normal((P, K)) + 1j * rng.standard_normal((P, K))) * scale).astype(np.complex64)
+
+
+def check(D, x, idx, pd, expect_unique_frac=None):
+    """Validity everywhere, exactness where the best atom is unique, PD of the chosen atom."""
+    D64 = D.astype(np.complex128)
+    x64 = x.reshape(D.shape[1], -1).astype(np.complex128)
+    nrm_x = np.linalg.norm(x64, axis=0)
+    sc = DM.normalised_scores(x64, D64)                         # [P][nvox]
+    s2 = (sc / np.where(nrm_x > 0, nrm_x, 1.0)[None]) ** 2
+    ref_idx, _ = DM.dictionary_match(x64, D64)
+    idx = idx.reshape(-1).astype(np.int64)
+    pd = pd.reshape(-1)
+    nvox = x64.shape[1]
+    cols = np.arange(nvox)
+    assert np.all((idx >= 0) & (idx < D.shape[0]))
+    best = s2[ref_idx, cols]
+    assert np.all(s2[idx, cols] >= best - SCORE_TOL), np.max(best - s2[idx, cols])
+    # unique: lead over other chunks > SCORE_TOL and over the rest of its chunk > FP32_GAP
+    chunk = ref_idx // 32
+    P = D.shape[0]
+    atom_chunk = np.arange(P) // 32
+    other = np.where(atom_chunk[:, None] == chunk[None, :], -np.inf, s2).max(axis=0)
+    same = s2.copy()
+    same[ref_idx, cols] = -np.inf
+    same = np.where(atom_chunk[:, None] == chunk[None, :], same, -np.inf).max(axis=0)
+    unique = (best - other > SCORE_TOL) & (best - same > FP32_GAP) & (nrm_x > 0)
+    assert np.array_equal(idx[unique], ref_idx[unique])
+    if expect_unique_frac is not None:
+        assert unique.mean() >= expect_unique_frac, unique.mean()
+    # PD of the atom the GPU chose: its least-squares scale d^H x / ||d||^2
+    d = D64[idx]
+    pd_ref = np.sum(d.conj() * x64.T, axis=1) / np.sum(np.abs(d) ** 2, axis=1)
+    den = np.maximum(np.abs(pd_ref), 1e-30)
+    nz = nrm_x > 0
+    assert np.max(np.abs(pd[nz] - pd_ref[nz]) / den[nz]) < PD_RTOL
+    assert np.all(pd[~nz] == 0) and np.all(idx[~nz] == 0)
+    return unique.mean()
+
+
+@pytest.mark.parametrize("K", [5, 1, 10])
+def test_planted_random_atoms_are_recovered_exactly(K):
+    from paper_2408_02367_gb300 import dm
+    P, nvox = 1000, 5000                                         # ragged: 1000 = 15 x 64 + 40, 5000 voxels
+    D = random_atoms(P, K, 21 + K)
+    x, p, pd_true = synth.dm_volume(D, nvox, noise=0.0, seed=22)
+    x[:, 17] = 0                                                 # a zero voxel
+    M = dm.DictionaryMatcher(_t(D), max_vox=nvox)
+    idx, pd = M.match(_t(x))
+    idx, pd = idx.cpu().numpy(), pd.cpu().numpy()
+    assert M.status() == 0
+    frac = check(D, x, idx, pd, expect_unique_frac=0.9 if K > 1 else None)
+    if K > 1:
+        sel = (np.arange(nvox) != 17)
+        assert np.mean(idx[sel] == p[sel]) >= frac - 1e-9
+    print(f"K={K}: unique fraction {frac:.3f}")
+
+
+def test_dense_mrf_dictionary_with_noise_and_qmaps():
+    from paper_2408_02367_gb300 import dm
+    f, params = synth.mrf_dictionary(480)
+    D, _ = synth.compress_dictionary(f, 5)
+    nvox = 4096 + 77
+    x, p, _ = synth.dm_volume(D, nvox, noise=0.02, seed=23)
+    M = dm.DictionaryMatcher(_t(D), max_vox=8192, params=_t(params))
+    idx, pd, qm = M.match(_t(x), qmap=True)
+    idx, pd, qm = idx.cpu().numpy(), pd.cpu().numpy(), qm.cpu().numpy()
+    assert M.status() == 0
+    frac = check(D, x, idx, pd)
+    assert np.array_equal(qm, params[idx.astype(np.int64)])
+    # repeatable bit for bit
+    idx2, pd2 = M.match(_t(x))
+    assert np.array_equal(idx2.cpu().numpy(), idx) and np.array_equal(pd2.cpu().numpy(), pd)
+    print(f"dense dictionary: unique fraction {frac:.3f}, P={D.shape[0]}")
+
+
+def test_voxel_shapes_tiny_and_empty_calls():
+    from paper_2408_02367_gb300 import dm
+    D = random_atoms(70, 3, 31)
+    M = dm.DictionaryMatcher(_t(D), max_vox=300)
+    x, p, _ = synth.dm_volume(D, 1, seed=32)
+    idx, pd = M.match(_t(x))
+    assert int(idx.cpu()[0]) == int(p[0])
+    vol = synth.random_complex((3, 5, 6, 7), 33)
+    idx, pd = M.match(_t(vol))
+    assert tuple(idx.shape) == (5, 6, 7)
+    check(D, vol, idx.cpu().numpy(), pd.cpu().numpy())
+    e = torch.empty((3, 0), dtype=torch.complex64, device="cuda")
+    idx, pd = M.match(e)
+    assert idx.numel() == 0
+    with pytest.raises(Exception):
+        M.match(_t(synth.random_complex((3, 301), 34)))              # more than max_vox
+    assert M.status() == 0
+    info = M.info()
+    assert info["P"] == 70 and info["K"] == 3 and info["ksteps"] == 1 and info["atom_tiles"] == 2
