@@ -18,7 +18,7 @@
 //     per voxel and half, the 32-atom chunk with the largest score (first
 //     chunk on ties).  The two halves are merged by the refine pass, so the
 //     epilogue warps never wait on each other.
-//  3. dm_refine: one warp per voxel takes the better of its two half results
+//  3. dm_refine: a warp per 4 voxels takes, for each, the better of its two half results
 //     (lower chunk on ties), recomputes the 32 inner products of that
 //     chunk in float32 from the float32 inputs and takes the argmax (lowest
 //     atom on ties) and PD.
@@ -240,8 +240,13 @@ __global__ void dm_prep_voxels(const float2* __restrict__ x, long long nvox, int
     store_row(xh + (v / BM) * (long long)(KS * 4096), (int)(v % BM), KS, e);
 }
 
-// One warp per voxel: lane l scores atom p = 32 * chunk + l in float32 and
-// the warp takes the argmax (lowest atom on ties) and PD = (d_p/||d_p||)^H x / ||d_p||.
+// Refine: a warp resolves RV voxels.  For voxel j the warp takes the better of
+// its two half results (lower chunk on ties); lane l scores atom
+// p = 32 * chunk + l in float32, and the warp takes the argmax (lowest atom on
+// ties) and PD = (d_p/||d_p||)^H x / ||d_p||.  The RV voxels' loads are
+// independent and issued together, so a warp has several round trips in flight.
+constexpr int RV = 4;
+
 __global__ void __launch_bounds__(256) dm_refine(const float2* __restrict__ x, long long nvox, int K,
                                                  const float* __restrict__ best_score,
                                                  const int* __restrict__ best_chunk,
@@ -249,45 +254,59 @@ __global__ void __launch_bounds__(256) dm_refine(const float2* __restrict__ x, l
                                                  long long P, const float2* __restrict__ params,
                                                  int* __restrict__ idx, float2* __restrict__ pd,
                                                  float2* __restrict__ qmap) {
-    const long long v = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (v >= nvox) return;
-    const float s0 = __ldg(best_score + v), s1 = __ldg(best_score + nvox + v);
-    const int c0 = __ldg(best_chunk + v), c1 = __ldg(best_chunk + nvox + v);
-    const int c = (s1 > s0 || (s1 == s0 && c1 < c0)) ? c1 : c0;
-    const long long p = (long long)c * CHUNK + lane;
-    float2 s = make_float2(0.f, 0.f);
-    float score = -1.f;
-    if (p < P) {
-        for (int k = 0; k < K; ++k) {
-            const float2 xk = __ldg(x + k * nvox + v);
-            const float2 d = __ldg(dhat + p * K + k);
-            s.x += d.x * xk.x + d.y * xk.y;
-            s.y += d.x * xk.y - d.y * xk.x;
-        }
-        score = s.x * s.x + s.y * s.y;
+    const long long vb = ((long long)blockIdx.x * 8 + (threadIdx.x >> 5)) * RV;
+    if (vb >= nvox) return;                                       // uniform over the warp
+    int cl = 0;                                                   // lane j < RV: chunk of voxel vb + j
+    if (lane < RV && vb + lane < nvox) {
+        const long long v = vb + lane;
+        const float s0 = __ldg(best_score + v), s1 = __ldg(best_score + nvox + v);
+        const int c0 = __ldg(best_chunk + v), c1 = __ldg(best_chunk + nvox + v);
+        cl = (s1 > s0 || (s1 == s0 && c1 < c0)) ? c1 : c0;
     }
-    float best = score;
-    int bl = lane;
+    long long p[RV];
+    float2 s[RV];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-        if (ov > best || (ov == best && ol < bl)) {
-            best = ov;
-            bl = ol;
+    for (int j = 0; j < RV; ++j) {
+        p[j] = (long long)__shfl_sync(0xffffffffu, cl, j) * CHUNK + lane;
+        s[j] = make_float2(0.f, 0.f);
+    }
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int j = 0; j < RV; ++j) {
+            if (vb + j < nvox && p[j] < P) {
+                const float2 xk = __ldg(x + k * nvox + vb + j);
+                const float2 d = __ldg(dhat + p[j] * K + k);
+                s[j].x += d.x * xk.x + d.y * xk.y;
+                s[j].y += d.x * xk.y - d.y * xk.x;
+            }
         }
     }
-    if (lane == bl) {
-        if (p < P) {
-            const float in = __ldg(inv_norm + p);
-            idx[v] = (int)p;
-            pd[v] = make_float2(s.x * in, s.y * in);
-            if (qmap) qmap[v] = __ldg(params + p);
-        } else {                       // a chunk past the last atom (not chosen by the score kernel)
-            idx[v] = 0;
-            pd[v] = make_float2(0.f, 0.f);
-            if (qmap) qmap[v] = __ldg(params);
+#pragma unroll
+    for (int j = 0; j < RV; ++j) {
+        float best = p[j] < P ? s[j].x * s[j].x + s[j].y * s[j].y : -1.f;
+        int bl = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ov > best || (ov == best && ol < bl)) {
+                best = ov;
+                bl = ol;
+            }
+        }
+        const long long v = vb + j;
+        if (lane == bl && v < nvox) {
+            if (p[j] < P) {
+                const float in = __ldg(inv_norm + p[j]);
+                idx[v] = (int)p[j];
+                pd[v] = make_float2(s[j].x * in, s[j].y * in);
+                if (qmap) qmap[v] = __ldg(params + p[j]);
+            } else {                   // a chunk past the last atom (not chosen by the score kernel)
+                idx[v] = 0;
+                pd[v] = make_float2(0.f, 0.f);
+                if (qmap) qmap[v] = __ldg(params);
+            }
         }
     }
 }
@@ -310,7 +329,7 @@ struct GemmArgs {
 // Re(2q), Re(2q+1), Im(2q), Im(2q+1): the squares of an atom pair in one
 // packed f32x2 multiply and fused multiply-add, then a three-input max.
 __device__ __forceinline__ float chunk_max(const float (&v)[64]) {
-    float m = 0.f;
+    float m[4] = {0.f, 0.f, 0.f, 0.f};          // four independent running maxima
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         unsigned long long re, im, s2;
@@ -320,9 +339,11 @@ __device__ __forceinline__ float chunk_max(const float (&v)[64]) {
         asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(s2) : "l"(im), "l"(s2));
         float sa, sb;
         asm("mov.b64 {%0, %1}, %2;" : "=f"(sa), "=f"(sb) : "l"(s2));
-        asm("max.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(m), "f"(sa), "f"(sb));
+        asm("max.f32 %0, %1, %2, %3;" : "=f"(m[q & 3]) : "f"(m[q & 3]), "f"(sa), "f"(sb));
     }
-    return m;
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m[0]), "f"(m[1]), "f"(m[2]));
+    return fmaxf(r, m[3]);
 }
 
 template <int KS>
@@ -643,7 +664,7 @@ int sdp_dm_match(sdp_dm_t dm, const void* x, int64_t nvox, int32_t* idx, void* p
         sdp::dm_score_kernel<1><<<grid, sdp::kThreadsG, smem, st>>>(a);
     else
         sdp::dm_score_kernel<2><<<grid, sdp::kThreadsG, smem, st>>>(a);
-    sdp::dm_refine<<<(unsigned)((nvox + 7) / 8), 256, 0, st>>>(xv, nvox, dm->K, dm->best_score, dm->best, dm->dhat,
+    sdp::dm_refine<<<(unsigned)((nvox + 8 * sdp::RV - 1) / (8 * sdp::RV)), 256, 0, st>>>(xv, nvox, dm->K, dm->best_score, dm->best, dm->dhat,
                                                                dm->inv_norm,
                                                                dm->P, dm->params, idx, static_cast<float2*>(pd),
                                                                reinterpret_cast<float2*>(qmap));
