@@ -56,9 +56,6 @@ struct sdp_plan_s {
     float2* tw = nullptr;    // [M1 | M2 | M3]
     int* inc = nullptr;
     SubProb* subs = nullptr;
-    int4* ichunks = nullptr;   // tiled interpolation: (bin, first sorted sample, count, 0)
-    int nichunks = 0;
-    bool interp_tiled = false;
     float2* partials = nullptr;
     int* counters = nullptr;
     int* status = nullptr;
@@ -357,32 +354,6 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     p->nsub = (int)subs.size();
     p->slots_per_b = slots;
 
-    // tiled interpolation: chunks of at most kIChunk sorted samples of one bin,
-    // usable when every sample's window lies in the tile of bs + W points from
-    // bin * bs - floor(W/2) on each axis and one channel's tile fits
-    bool tiled_ok = interp_tile_channels(W, bs, K) >= 1;
-    for (long long sidx = 0; sidx < J && tiled_ok; ++sidx) {
-        const int j = perm[sidx];
-        long long bi = sbin[j];
-        int bc[3];
-        for (int a = 2; a >= 0; --a) {
-            bc[a] = (int)(bi % p->nb[a]);
-            bi /= p->nb[a];
-        }
-        for (int a = 0; a < 3; ++a) {
-            const int r = m0[(size_t)j * 3 + a] - (bc[a] * bs[a] - W / 2);
-            if (r < 0 || r > bs[a]) tiled_ok = false;
-        }
-    }
-    std::vector<int4> ich;
-    for (long long b = 0; b < nbins && tiled_ok; ++b)
-        for (long long c0 = cnt[b]; c0 < cnt[b + 1]; c0 += kIChunk)
-            ich.push_back(make_int4((int)b, (int)c0, (int)std::min<long long>(kIChunk, cnt[b + 1] - c0), 0));
-    if (ich.size() >= (1ULL << 31)) tiled_ok = false;
-    if (const char* ev = std::getenv("SDP_INTERP_GATHER")) tiled_ok = tiled_ok && std::atoi(ev) == 0;
-    p->interp_tiled = tiled_ok;
-    p->nichunks = tiled_ok ? (int)ich.size() : 0;
-
     // ---- device memory ----
     const size_t Kz = (size_t)K;
     SDP_TRY(dev_alloc(p, &p->pts, (size_t)J));
@@ -394,7 +365,6 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_TRY(dev_alloc(p, &p->tw, tw.size()));
     SDP_TRY(dev_alloc(p, &p->inc, inc.size()));
     SDP_TRY(dev_alloc(p, &p->subs, subs.size()));
-    if (p->nichunks > 0) SDP_TRY(dev_alloc(p, &p->ichunks, ich.size()));
     const size_t P = (size_t)bs[0] * bs[1] * bs[2];
     SDP_TRY(dev_alloc(p, &p->partials, (size_t)std::max(slots, 1LL) * P * Kz * p->maxB));
     SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB * ((K + 7) / 8)));
@@ -418,10 +388,6 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     SDP_CUDA(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->inc, inc.data(), inc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(SubProb), cudaMemcpyHostToDevice, st));
-    if (p->nichunks > 0) {
-        SDP_CUDA(cudaMemcpyAsync(p->ichunks, ich.data(), ich.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-        SDP_CUDA(interp_tiled_configure(W));
-    }
     SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * ((K + 7) / 8) * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
@@ -488,15 +454,6 @@ int check_call(const sdp_plan_s* p, const void* in, const int32_t* coil_idx, int
     return SDP_OK;
 }
 
-// Interpolation of the plan's grid buffer: the tiled kernel when the plan set it up, else the gather kernel.
-cudaError_t interp_any(sdp_plan_s* p, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
-    const Geo& g = p->geo;
-    if (p->interp_tiled)
-        return launch_interp_tiled(g, p->bs, p->nb, p->ichunks, p->nichunks, p->pts, p->tframe, p->wts, p->V, p->bufA,
-                                   B, k0, nk, y, accumulate, st);
-    return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk, y, accumulate, st);
-}
-
 int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, int k0, int nk, void* y,
                  int accumulate, cudaStream_t st) {
     SDP_TRY(check_call(p, x, coil_idx, B, k0, nk, y));
@@ -516,7 +473,8 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
         return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3, BK, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
-        return interp_any(p, B, k0, nk, static_cast<float2*>(y), accumulate, st);
+        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y),
+                             accumulate, st);
     }));
     return SDP_OK;
 }
@@ -733,7 +691,8 @@ int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* st
                              p->counters, p->nbins, st);
     }));
     return run(p, ST_INTERP, st, [&] {
-        return interp_any(p, B, 0, g.K, static_cast<float2*>(out), 0, st);
+        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K, static_cast<float2*>(out), 0,
+                             st);
     });
 }
 

@@ -18,8 +18,6 @@
 // B coils and K channels; the W taps along axis 3 are adjacent lanes reading
 // adjacent addresses.  Each lane folds V[t, k] into its partial sum and a
 // butterfly reduction leaves the sample value in lane 0.
-#include <algorithm>
-
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -27,14 +25,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
-constexpr long long kInterpTileBytes = 100 * 1024;   // shared memory of a tiled-interpolation CTA, at most
 
 __device__ __forceinline__ int wrap1(int i, int M) { return i < 0 ? i + M : (i >= M ? i - M : i); }
-// i mod M in [0, M) for any i (a tile can span more than one period of a small grid)
-__device__ __forceinline__ int wrapm(int i, int M) {
-    const int r = i % M;
-    return r < 0 ? r + M : r;
-}
 
 __global__ void kb_weights_kernel(Geo g, const float4* __restrict__ pts, float* __restrict__ wts) {
     const int W = g.W;
@@ -138,111 +130,6 @@ __global__ void __launch_bounds__(kThreads) interp_kernel(Geo g, const float4* _
     }
 }
 
-// ---------------------------------------------------------------------------
-// Tiled interpolation.  Samples are stored sorted by the bin (bs1 x bs2 x bs3
-// grid points) that holds their coordinate, so the window of every sample of
-// bin (b1, b2, b3) lies in the tile of TL_d = bs_d + W grid points starting at
-// o_d = b_d bs_d - floor(W/2) (the plan checks this for every sample).  A CTA
-// takes one chunk of at most kIChunk samples of one bin for one coil: it copies
-// the tile of every channel of a group into shared memory (periodic wrap
-// resolved once, while copying), then each warp interpolates whole samples
-// from shared memory, one tap pair per lane as in the gather kernel.  The
-// grid is read once per chunk instead of once per tap, and the taps of a
-// sample are shared-memory reads with at most two wavefronts per warp access.
-// ---------------------------------------------------------------------------
-template <int W>
-__global__ void __launch_bounds__(kThreads) interp_tiled_kernel(
-    Geo g, int3 bs, int3 nb, const int4* __restrict__ chunks, const float4* __restrict__ pts,
-    const int* __restrict__ tframe, const float* __restrict__ wts, const float2* __restrict__ V,
-    const float2* __restrict__ grids, int k0, int nk, int nkg, float2* __restrict__ y, int accumulate) {
-    constexpr int W3 = W * W * W;
-    constexpr int NIT = (W3 + 31) / 32;
-    extern __shared__ float2 tile[];                       // [nkg][TL1][TL2][TL3], then per-sample partials
-    const int TL1 = bs.x + W, TL2 = bs.y + W, TL3 = bs.z + W;
-    const int TP = TL1 * TL2 * TL3;
-    float2* part = tile + (size_t)nkg * TP;                // [count] partial sums across channel groups
-    const int4 ch = __ldg(chunks + blockIdx.x);            // (bin, first sorted sample, count, -)
-    const int b = blockIdx.y;
-    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
-    const long long G = (long long)M1 * M2 * M3;
-    const int bb3 = ch.x % nb.z, bb12 = ch.x / nb.z, bb2 = bb12 % nb.y, bb1 = bb12 / nb.y;
-    const int o1 = bb1 * bs.x - W / 2, o2 = bb2 * bs.y - W / 2, o3 = bb3 * bs.z - W / 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool multi = nkg < nk;
-    for (int c0 = 0; c0 < nk; c0 += nkg) {
-        const int ng = min(nkg, nk - c0);
-        __syncthreads();                                   // the previous group's tile is no longer read
-        for (int e = threadIdx.x; e < ng * TP; e += kThreads) {
-            const int c = e / TP, r = e - c * TP;
-            const int r3 = r % TL3, r12 = r / TL3, r2 = r12 % TL2, r1 = r12 / TL2;
-            const int i1 = wrapm(o1 + r1, M1), i2 = wrapm(o2 + r2, M2), i3 = wrapm(o3 + r3, M3);
-            tile[e] = __ldg(grids + ((long long)b * nk + c0 + c) * G + ((long long)i1 * M2 + i2) * M3 + i3);
-        }
-        __syncthreads();
-        for (int q = warp; q < ch.z; q += kThreads / 32) {
-            const long long s = (long long)ch.y + q;
-            const float4 p = __ldg(pts + s);
-            const int t = __ldg(tframe + s);
-            const int r01 = (int)ceilf(p.x - g.halfW) - o1;
-            const int r02 = (int)ceilf(p.y - g.halfW) - o2;
-            const int r03 = (int)ceilf(p.z - g.halfW) - o3;
-            const float wv = lane < 3 * W ? __ldg(wts + s * (3 * W) + lane) : 0.f;
-            float wt[NIT];
-            int off[NIT];
-#pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int tau = lane + 32 * it;
-                const bool valid = tau < W3;
-                const int tc = valid ? tau : 0;
-                const int a1 = tc / (W * W), a2 = (tc / W) % W, a3 = tc % W;
-                const float w1 = __shfl_sync(kFull, wv, a1);
-                const float w2 = __shfl_sync(kFull, wv, W + a2);
-                const float w3 = __shfl_sync(kFull, wv, 2 * W + a3);
-                wt[it] = valid ? w1 * w2 * w3 : 0.f;
-                off[it] = ((r01 + a1) * TL2 + (r02 + a2)) * TL3 + (r03 + a3);
-            }
-            const float2* Vt = V + (long long)t * g.K + k0 + c0;
-            float ax = 0.f, ay = 0.f;
-            for (int c = 0; c < ng; ++c) {
-                const float2* tc_ = tile + (size_t)c * TP;
-                float sx = 0.f, sy = 0.f;
-#pragma unroll
-                for (int it = 0; it < NIT; ++it) {
-                    const float2 gv = tc_[off[it]];
-                    sx = fmaf(wt[it], gv.x, sx);
-                    sy = fmaf(wt[it], gv.y, sy);
-                }
-                const float2 v = __ldg(Vt + c);
-                ax += v.x * sx - v.y * sy;
-                ay += v.x * sy + v.y * sx;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ax += __shfl_xor_sync(kFull, ax, o);
-                ay += __shfl_xor_sync(kFull, ay, o);
-            }
-            if (lane == 0) {
-                if (multi) {
-                    if (c0 > 0) {
-                        ax += part[q].x;
-                        ay += part[q].y;
-                    }
-                    part[q] = make_float2(ax, ay);
-                }
-                if (c0 + ng >= nk) {
-                    float2* dst = y + (long long)b * g.J + __float_as_int(p.w);
-                    if (accumulate) {
-                        const float2 old = *dst;
-                        ax += old.x;
-                        ay += old.y;
-                    }
-                    *dst = make_float2(ax, ay);
-                }
-            }
-        }
-    }
-}
-
 template <int W, int CK>
 cudaError_t launch_wk(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
                       const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
@@ -275,68 +162,6 @@ cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaS
     if (nblk > 65536) nblk = 65536;
     kb_weights_kernel<<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, wts);
     return cudaGetLastError();
-}
-
-int interp_tile_channels(int W, const int bs[3], int nk) {
-    const long long tp = (long long)(bs[0] + W) * (bs[1] + W) * (bs[2] + W);
-    const long long budget = kInterpTileBytes - (long long)kIChunk * 8;
-    return (int)std::min<long long>(budget / (tp * 8), nk);
-}
-
-size_t interp_tile_smem(int W, const int bs[3], int nkg) {
-    const size_t tp = (size_t)(bs[0] + W) * (bs[1] + W) * (bs[2] + W);
-    return (size_t)nkg * tp * 8 + (size_t)kIChunk * 8;
-}
-
-template <int W>
-cudaError_t launch_tiled_w(const Geo& g, const int bs[3], const int nb[3], const int4* chunks, int nchunks,
-                           const float4* pts, const int* tframe, const float* wts, const float2* V,
-                           const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
-    const int nkg = interp_tile_channels(W, bs, nk);
-    const size_t smem = interp_tile_smem(W, bs, nkg);
-    interp_tiled_kernel<W><<<dim3((unsigned)nchunks, (unsigned)B), kThreads, smem, st>>>(
-        g, make_int3(bs[0], bs[1], bs[2]), make_int3(nb[0], nb[1], nb[2]), chunks, pts, tframe, wts, V, grids, k0,
-        nk, nkg, y, accumulate);
-    return cudaGetLastError();
-}
-
-// Every launch of the tiled kernel asks for at most kInterpTileBytes of shared
-// memory (interp_tile_channels keeps it there), so the attribute is always set
-// to that bound: a later plan never lowers it below an earlier plan's need.
-template <int W>
-cudaError_t configure_w() {
-    return cudaFuncSetAttribute(interp_tiled_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kInterpTileBytes);
-}
-
-cudaError_t interp_tiled_configure(int W) {
-    switch (W) {
-        case 2: return configure_w<2>();
-        case 3: return configure_w<3>();
-        case 4: return configure_w<4>();
-        case 5: return configure_w<5>();
-        case 6: return configure_w<6>();
-        case 7: return configure_w<7>();
-        case 8: return configure_w<8>();
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_interp_tiled(const Geo& g, const int bs[3], const int nb[3], const int4* chunks, int nchunks,
-                                const float4* pts, const int* tframe, const float* wts, const float2* V,
-                                const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
-                                cudaStream_t st) {
-    if (nchunks == 0) return cudaSuccess;
-    switch (g.W) {
-        case 2: return launch_tiled_w<2>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 3: return launch_tiled_w<3>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 4: return launch_tiled_w<4>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 5: return launch_tiled_w<5>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 6: return launch_tiled_w<6>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 7: return launch_tiled_w<7>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 8: return launch_tiled_w<8>(g, bs, nb, chunks, nchunks, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,

@@ -63,25 +63,11 @@ struct Geo {
     float halfW;
 };
 
-// Samples per chunk of the tiled interpolation (one CTA per chunk and coil).
-constexpr int kIChunk = 256;
-
 // Compile-time channel-group size of the interpolation and spread kernels for
 // nk channels: exact for 1..5, groups of 8 above.
 inline int channel_group(int nk) { return nk <= 5 ? nk : 8; }
 
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
-// Tiled interpolation: chunks = (bin, first sorted sample, count, 0) of at most
-// kIChunk samples; every sample's window must lie in its bin's tile (checked by
-// the plan).  interp_tile_channels gives the channels per shared-memory group
-// (0: the tile of one channel does not fit, use launch_interp).
-int interp_tile_channels(int W, const int bs[3], int nk);
-size_t interp_tile_smem(int W, const int bs[3], int nkg);
-cudaError_t interp_tiled_configure(int W);   // once per plan, before any capture
-cudaError_t launch_interp_tiled(const Geo& g, const int bs[3], const int nb[3], const int4* chunks, int nchunks,
-                                const float4* pts, const int* tframe, const float* wts, const float2* V,
-                                const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
-                                cudaStream_t st);
 cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int* status,

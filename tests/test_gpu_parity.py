@@ -133,39 +133,6 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
 
 
-def test_gather_interpolation_matches_oracle_and_tiled(tmp_path):
-    """The per-sample gather kernel (forced by SDP_INTERP_GATHER=1 in a child process)
-    against the oracle, and against the shared-memory tiled kernel the plan uses by default."""
-    import os
-    import subprocess
-    import sys
-    code = (
-        "import numpy as np, torch, sys\n"
-        "sys.path.insert(0, '.')\n"
-        "from tests.test_gpu_parity import make_case, gpu_op, t, rel, FP32_BOUND\n"
-        "from oracle import nufft as O\n"
-        "out = sys.argv[1]\n"
-        "for n, W, s in [((20, 18, 16), 4, 1.25), ((16, 12, 10), 6, 2.0)]:\n"
-        "    c = make_case(n, W, s, 3, 3, 10, 1, 400, [2, 0])\n"
-        "    geo = O.Geometry(c['n'], W, s)\n"
-        "    A = gpu_op(c)\n"
-        "    y = A.forward(t(c['x']), t(c['coils'])).cpu().numpy()\n"
-        "    e = rel(y, O.gridding_forward(geo, c['x'], c['S'], c['V'], c['omega'], c['frame'], c['coils']))\n"
-        "    np.save(out + '/y_%d.npy' % W, y)\n"
-        "    print(W, e)\n"
-        "    assert e < FP32_BOUND\n")
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    for mode in ("1", "0"):
-        d = tmp_path / mode
-        d.mkdir()
-        env = dict(os.environ, SDP_INTERP_GATHER=mode)
-        r = subprocess.run([sys.executable, "-c", code, str(d)], cwd=root, env=env, capture_output=True, text=True,
-                           timeout=600)
-        assert r.returncode == 0, r.stdout + r.stderr
-    for W in (4, 6):
-        assert rel(np.load(tmp_path / "1" / f"y_{W}.npy"), np.load(tmp_path / "0" / f"y_{W}.npy")) < 1e-6
-
-
 def test_adjoint_identity_on_gpu():
     c = make_case((24, 20, 28), 4, 1.25, 5, 4, 30, 1, 400, [3, 1, 2])
     A = gpu_op(c)
