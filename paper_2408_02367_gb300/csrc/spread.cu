@@ -64,11 +64,20 @@ struct SpreadArgs {
 constexpr int B1 = 8, B2 = 4, B3 = 8;
 constexpr int BP = B1 * B2 * B3;
 
+// Two packed (Re, Im) accumulators as one float4 (Re0, Im0, Re1, Im1).
+__device__ __forceinline__ float4 pair4(unsigned long long a, unsigned long long b) {
+    float4 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.z), "=f"(r.w) : "l"(b));
+    return r;
+}
+
 template <int W, int NK>
 __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     constexpr int NW = 3 * W;
-    constexpr int NP = B1 + B2 + B3;          // staged weights per incidence: one per bin position
-    __shared__ float psm[32 * NP];            // [incidence][x1 (8) | x2 (4) | x3 (8)], 0 outside the window
+    constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
+    __shared__ float psm[32 * NP];            // [incidence][x1 (8) | x2 (4)], 0 outside the window
+    __shared__ float2 p3sm[32 * B3];          // [incidence][x3]: (w3, w3), 0 outside the window
     __shared__ unsigned msm[32];              // axis-3 positions the window covers (bit x3)
     __shared__ float2 csm[32 * NK];
     const Geo& g = a.g;
@@ -84,11 +93,12 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
     const long long G = (long long)M1 * M2 * M3;
 
-    float2 acc[B3][NK];
+    // accumulators as packed (Re, Im) pairs for the f32x2 multiply-adds
+    unsigned long long acc[B3][NK];
 #pragma unroll
     for (int x3 = 0; x3 < B3; ++x3)
 #pragma unroll
-        for (int q = 0; q < NK; ++q) acc[x3][q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < NK; ++q) acc[x3][q] = 0ull;
 
     const float2* yb = a.y + (long long)b * g.J;
     const float sc = a.scale ? __ldg(a.scale) : 1.f;
@@ -141,7 +151,7 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
                 float v = 0.f;
 #pragma unroll
                 for (int q = 0; q < W; ++q) v = aa == q ? wl[2 * W + q] : v;
-                pw[B1 + B2 + x] = v;
+                p3sm[lane * B3 + x] = make_float2(v, v);
                 mask |= ((unsigned)aa < (unsigned)W ? 1u : 0u) << x;
             }
             msm[lane] = mask;
@@ -157,18 +167,22 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
             const float* pw = psm + i * NP;
             const unsigned mask = msm[i];
             const float w12 = pw[x1] * pw[B1 + x2];
-            float2 c[NK];
+            unsigned long long w12p;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(w12p) : "f"(w12));
+            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(csm + i * NK);
+            const unsigned long long* wp3 = reinterpret_cast<const unsigned long long*>(p3sm + i * B3);
+            unsigned long long c[NK];
 #pragma unroll
-            for (int q = 0; q < NK; ++q) c[q] = csm[i * NK + q];
+            for (int q = 0; q < NK; ++q) c[q] = cp[q];
 #pragma unroll
             for (int x3 = 0; x3 < B3; ++x3) {
                 if (mask & (1u << x3)) {                 // the same for every lane
-                    const float w = w12 * pw[B1 + B2 + x3];
+                    // w = w12 * w3 and acc += w * c, both components at once (round to nearest
+                    // per component: the same arithmetic as two scalar multiplies and FMAs)
+                    unsigned long long w;
+                    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(w) : "l"(w12p), "l"(wp3[x3]));
 #pragma unroll
-                    for (int q = 0; q < NK; ++q) {
-                        acc[x3][q].x = fmaf(w, c[q].x, acc[x3][q].x);
-                        acc[x3][q].y = fmaf(w, c[q].y, acc[x3][q].y);
-                    }
+                    for (int q = 0; q < NK; ++q) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[x3][q]) : "l"(w), "l"(c[q]));
                 }
             }
         }
@@ -187,7 +201,7 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
                 for (int x3 = 0; x3 < B3; x3 += 2)
                     if (lo3 + x3 < M3)
                         *reinterpret_cast<float4*>(gcol + q * G + x3) =
-                            make_float4(acc[x3][q].x, acc[x3][q].y, acc[x3 + 1][q].x, acc[x3 + 1][q].y);
+                            pair4(acc[x3][q], acc[x3 + 1][q]);
         }
         return;
     }
@@ -200,7 +214,7 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
 #pragma unroll
         for (int x3 = 0; x3 < B3; x3 += 2)
             part[(q * BP + lane * B3 + x3) / 2] =
-                make_float4(acc[x3][q].x, acc[x3][q].y, acc[x3 + 1][q].x, acc[x3 + 1][q].y);
+                pair4(acc[x3][q], acc[x3 + 1][q]);
     __threadfence();
     __syncwarp();
     int last = 0;
