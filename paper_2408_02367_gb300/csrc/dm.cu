@@ -9,7 +9,8 @@
 //  2. dm_score_kernel: a persistent tcgen05 GEMM.  One CTA per SM walks pairs
 //     of voxel tiles; for each pair it streams the fp16 atom tiles (64 atoms =
 //     128 rows (Re-column, Im-column) each) through a shared-memory ring with
-//     bulk copies, issues M=128 x N=128 x K=16 MMAs into fp32 accumulators in
+//     bulk copies, two threads (one per voxel tile) issue M=128 x N=128 x K=16
+//     MMAs into fp32 accumulators in
 //     tensor memory (two buffers x two voxel tiles x 128 columns = all 512
 //     columns), and sixteen epilogue warps read the accumulators with
 //     tcgen05.ld (one warp per voxel tile, 64-column half and lane quarter),
@@ -123,22 +124,16 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld_x64(uint32_t taddr, float (&v)[64]) {
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32]) {
     uint32_t* r = reinterpret_cast<uint32_t*>(v);
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
 }
@@ -325,13 +320,13 @@ struct GemmArgs {
     int* status;
 };
 
-// Largest |d^H x|^2 over the 32 atoms of 64 accumulator columns laid out
+// Largest |d^H x|^2 over the 16 atoms of 32 accumulator columns laid out
 // Re(2q), Re(2q+1), Im(2q), Im(2q+1): the squares of an atom pair in one
 // packed f32x2 multiply and fused multiply-add, then a three-input max.
-__device__ __forceinline__ float chunk_max(const float (&v)[64]) {
+__device__ __forceinline__ float half_max(const float (&v)[32]) {
     float m[4] = {0.f, 0.f, 0.f, 0.f};          // four independent running maxima
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 8; ++q) {
         unsigned long long re, im, s2;
         asm("mov.b64 %0, {%1, %2};" : "=l"(re) : "f"(v[4 * q]), "f"(v[4 * q + 1]));
         asm("mov.b64 %0, {%1, %2};" : "=l"(im) : "f"(v[4 * q + 2]), "f"(v[4 * q + 3]));
@@ -351,11 +346,13 @@ __host__ __device__ constexpr uint32_t tile_bytes() { return KS * 4096u; }
 
 template <int KS>
 constexpr int score_smem_bytes() {
-    return 1024 + (2 * VT + NB) * (int)tile_bytes<KS>() + (5 + 2 * NB + 2 * NACC) * 8 + 8;
+    return 1024 + (2 * VT + NB) * (int)tile_bytes<KS>() + (4 + 2 * NB + 2 * VT * NACC + VT) * 8 + 8;
 }
 
-// Warp roles: warp 0 lane 0 copies tiles in (bulk copies), warp 1 lane 0
-// issues the MMAs, warp 2 owns the tensor memory, warps 4..19 are the
+// Warp roles: warp 0 lane 0 copies tiles in (bulk copies), lane 0 of warp 1
+// (voxel tile 0) and of warp 3 (voxel tile 1) issue the MMAs, each with its own
+// accumulator barriers so the two wait/issue/commit chains run side by side,
+// warp 2 owns the tensor memory, warps 4..19 are the
 // epilogue (warp 4 + 8u + 4h + q reads lanes 32q..32q+31, columns 64h..64h+63
 // of voxel tile u).
 template <int KS>
@@ -370,27 +367,27 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
     uint64_t* a_empty = bars + 2;                      // [2]
     uint64_t* b_full = bars + 4;                       // [NB]
     uint64_t* b_empty = bars + 4 + NB;                 // [NB]
-    uint64_t* acc_full = bars + 4 + 2 * NB;            // [NACC]
-    uint64_t* acc_empty = acc_full + NACC;             // [NACC]
-    uint64_t* mma_done = acc_empty + NACC;             // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+    uint64_t* acc_full = bars + 4 + 2 * NB;            // [VT][NACC]
+    uint64_t* acc_empty = acc_full + VT * NACC;        // [VT][NACC]
+    uint64_t* mma_done = acc_empty + VT * NACC;        // [VT]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + VT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(a_full + i), 1);
-            mbar_init(smem_u32(a_empty + i), 1);
+            mbar_init(smem_u32(a_empty + i), VT);               // both MMA threads release a voxel stage
         }
-        for (int i = 0; i < NACC; ++i) {
+        for (int i = 0; i < VT * NACC; ++i) {
             mbar_init(smem_u32(acc_full + i), 1);
-            mbar_init(smem_u32(acc_empty + i), kEpiWarps);
+            mbar_init(smem_u32(acc_empty + i), kEpiWarps / VT); // the epilogue warps of one voxel tile
         }
         for (int i = 0; i < NB; ++i) {
             mbar_init(smem_u32(b_full + i), 1);
-            mbar_init(smem_u32(b_empty + i), 1);
+            mbar_init(smem_u32(b_empty + i), VT);               // both MMA threads release an atom tile
         }
-        mbar_init(smem_u32(mma_done), 1);
+        for (int i = 0; i < VT; ++i) mbar_init(smem_u32(mma_done + i), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -438,11 +435,14 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
                 if (nb > s)
                     mbar_wait(smem_u32(b_full + s), (uint32_t)(((nb - 1 - s) / NB) & 1), abort_flag, g.status, false);
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == 3) {
         if (lane == 0) {
+            const int u = warp == 1 ? 0 : 1;  // this thread's voxel tile of the pair
             // kind::f16 instruction descriptor: fp32 accumulator, fp16 A and B, both
             // K-major, N = BN, M = BM
             const uint32_t idesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+            uint64_t* accf = acc_full + u * NACC;
+            uint64_t* acce = acc_empty + u * NACC;
             long long nb = 0;
             bool ok = true;
             for (int i = 0; i < nsteps && ok; ++i) {
@@ -453,31 +453,27 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
                     const int s = (int)(nb % NB);
                     const int b = (int)(nb % NACC);
                     if (!mbar_wait(smem_u32(b_full + s), (uint32_t)((nb / NB) & 1), abort_flag, g.status, true) ||
-                        !mbar_wait(smem_u32(acc_empty + b), (uint32_t)((nb / NACC) & 1) ^ 1u, abort_flag, g.status,
+                        !mbar_wait(smem_u32(acce + b), (uint32_t)((nb / NACC) & 1) ^ 1u, abort_flag, g.status,
                                    true)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)((b * VT + u) * BN);
 #pragma unroll
-                    for (int u = 0; u < VT; ++u) {
-                        const uint32_t d = tmem + (uint32_t)((b * VT + u) * BN);
-#pragma unroll
-                        for (int ks = 0; ks < KS; ++ks) {
-                            const uint64_t ad =
-                                smem_desc(smem_u32(sA + (sa * VT + u) * TB + ks * 256), 128, KS * 256);
-                            const uint64_t bd = smem_desc(smem_u32(sB + s * TB + ks * 256), 128, KS * 256);
-                            tc_mma_f16(d, ad, bd, idesc, ks > 0 ? 1u : 0u);
-                        }
+                    for (int ks = 0; ks < KS; ++ks) {
+                        const uint64_t ad = smem_desc(smem_u32(sA + (sa * VT + u) * TB + ks * 256), 128, KS * 256);
+                        const uint64_t bd = smem_desc(smem_u32(sB + s * TB + ks * 256), 128, KS * 256);
+                        tc_mma_f16(d, ad, bd, idesc, ks > 0 ? 1u : 0u);
                     }
                     tc_commit(smem_u32(b_empty + s));
-                    tc_commit(smem_u32(acc_full + b));
+                    tc_commit(smem_u32(accf + b));
                 }
                 if (ok) tc_commit(smem_u32(a_empty + sa));
             }
-            // every MMA issued has completed before the tensor memory is freed
-            tc_commit(smem_u32(mma_done));
-            mbar_wait(smem_u32(mma_done), 0, abort_flag, g.status, false);
+            // every MMA this thread issued has completed before the tensor memory is freed
+            tc_commit(smem_u32(mma_done + u));
+            mbar_wait(smem_u32(mma_done + u), 0, abort_flag, g.status, false);
         }
     } else if (warp >= 4) {
         const int eg = warp - 4;
@@ -493,7 +489,7 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             int bestc = 0;
             for (int t = 0; t < ntiles; ++t, ++nb) {
                 const int b = (int)(nb % NACC);
-                const bool w = mbar_wait(smem_u32(acc_full + b), (uint32_t)((nb / NACC) & 1), abort_flag, g.status,
+                const bool w = mbar_wait(smem_u32(acc_full + u * NACC + b), (uint32_t)((nb / NACC) & 1), abort_flag, g.status,
                                          true);
                 if (!__all_sync(0xffffffffu, w)) {     // warp-uniform: tcgen05.ld is .sync.aligned
                     ok = false;
@@ -502,13 +498,18 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
                 tc_fence_after();
                 const uint32_t taddr =
                     tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((b * VT + u) * BN + h * 64);
-                float v[64];
-                tmem_ld_x64(taddr, v);
+                // two 32-column loads: the maximum of the first half is formed while
+                // the second half is still on its way from tensor memory
+                float va[32], vb[32];
+                tmem_ld_x32(taddr, va);
+                tmem_wait_ld();
+                tmem_ld_x32(taddr + 32, vb);
+                const float ma = half_max(va);
                 tmem_wait_ld();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
-                const float m = chunk_max(v);
+                if (lane == 0) mbar_arrive(smem_u32(acc_empty + u * NACC + b));
+                const float m = fmaxf(ma, half_max(vb));
                 if (m > best) {
                     best = m;
                     bestc = 2 * t + h;
