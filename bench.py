@@ -176,11 +176,12 @@ def stage_bytes(w, B, M, ninc):
 
 
 # DRAM bytes (read + write) of one launch of each kernel on the vol128_w4
-# workload (B=2, K=5), from one `ncu --set full` capture each (profiles/
-# kernels_vol128_w4.md), keyed with a hash of the kernel's source file at
-# capture time: a kernel whose source has changed since reports null.
+# workload (B=2, K=5), from one `ncu --set full` capture each (profiles/),
+# keyed with a hash of the kernel's source file at capture time (and, for the
+# spread, its bin shape): a kernel whose source has changed since reports null.
 NCU_TRAFFIC = {
-    "spread": ("spread.cu", "97c5eb57bf88457d", (98.738688 + 306.551552) * 1e6),
+    ("spread", (8, 4, 8)): ("spread_impl.cuh", "73193d4934f04666", (98.695936 + 306.676480) * 1e6),
+    ("spread", (8, 4, 4)): ("spread_impl.cuh", "73193d4934f04666", (98.389760 + 292.594944) * 1e6),
     "interp": ("interp.cu", "c361be2ea2ecdce8", (242.524672 + 8.102144) * 1e6),
     "fwd_prologue_fft3": ("fft2.cu", "1b4f0646957d9724", (117.494016 + 156.42752) * 1e6),
     "adj_ifft3_epilogue": ("fft2.cu", "1b4f0646957d9724", (243.298304 + 62.400768) * 1e6),
@@ -194,11 +195,12 @@ def source_hash(fname):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(stage, workload_name, B):
-    """ncu DRAM bytes per launch of `stage`, if captured for this workload and the current source."""
-    if workload_name != "vol128_w4" or B != 2 or stage not in NCU_TRAFFIC:
+def measured_traffic(stage, workload_name, B, bins=(8, 4, 8)):
+    """ncu DRAM bytes per launch of `stage`, if captured for this workload, bin shape and the current source."""
+    key = (stage, tuple(bins)) if stage == "spread" else stage
+    if workload_name != "vol128_w4" or B != 2 or key not in NCU_TRAFFIC:
         return None
-    fname, h, nbytes = NCU_TRAFFIC[stage]
+    fname, h, nbytes = NCU_TRAFFIC[key]
     return nbytes if source_hash(fname) == h else None
 
 
@@ -318,7 +320,14 @@ def run_native(args):
 
     x_true, S, V, omega, frame = synth.make_problem(w)
     x_hat = synth.ellipsoid_phantom(w.n, w.K, seed=1)
-    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=max(B, 1), device=dev)
+    # kernel shapes: the framework's autotuner on this trajectory and volume
+    tuning, tune_table = None, None
+    if not args.no_tune:
+        from paper_2408_02367_gb300 import tune
+        tuning, tune_table = tune.autotune(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=max(B, 1), B=B,
+                                           reps=7, device=dev)
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=max(B, 1), device=dev,
+                         tuning=tuning)
     info = A.info()
     M = (info["M1"], info["M2"], info["M3"])
 
@@ -609,13 +618,16 @@ def run_native(args):
                        "speedup_vs_graph": plain_ms / graph_ms},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": measured_traffic(dom, w.name, B),
+                     "traffic": measured_traffic(dom, w.name, B, A.tuning["spread_bins"]),
                      "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches_per_step": per_step},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
         "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},
         "operator_rows": rows,
+        "tuning": {"chosen": dict(A.tuning, spread_bins=list(A.tuning["spread_bins"])),
+                   "autotuner": tune_table, "note": "forward + adjoint of one coil minibatch per candidate, "
+                   "median of 7 with L2 flushed; every candidate checked against the first to 1e-5"},
         "cpu_baseline": cpu,
         "e2e": {"value": ws * B * w.J / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3, "steps": n_e2e},
@@ -636,6 +648,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="vol128_w4", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default kernel shapes instead of the autotuner's")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

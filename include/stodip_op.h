@@ -104,6 +104,38 @@ typedef struct {
  */
 int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
 
+/*
+ * Kernel-shape choices of a plan, for an autotuner (the paper has no
+ * counterpart: it leaves the NUFFT's internals to a library).  Every choice
+ * computes the same operator; they differ in speed and in the order of
+ * floating-point sums only.
+ *   spread_bins   grid points per spread bin (axis 1, 2, 3): {8, 4, 8} (default,
+ *                 a lane per 8-point axis-3 column) or {8, 4, 4} (half-depth
+ *                 columns: fewer registers per lane, more incidences per sample).
+ *   spread_chunk  incidences per spread subproblem, 32 .. 65536 (default 512):
+ *                 bounds the work of one CTA on the dense k-space centre.
+ *   fft_engine    0: two-pass register FFTs where the length has one (default),
+ *                 1: the radix-2/3/4/5 Stockham kernels for every length.
+ *   reserved      must be 0.
+ */
+typedef struct {
+    int32_t spread_bins[3];
+    int32_t spread_chunk;
+    int32_t fft_engine;
+    int32_t reserved[3];
+} sdp_tuning;
+
+/*
+ * sdp_plan_create with the kernel shapes of `tuning` (NULL: the defaults, with
+ * the SDP_SPREAD_CHUNK and SDP_FFT_GENERIC environment overrides honoured).
+ * SDP_ERR_UNSUPPORTED for a bin shape without a kernel, SDP_ERR_INVALID_ARG
+ * for other values out of range (checked on the host before any device work).
+ */
+int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* desc, const sdp_tuning* tuning, void* stream);
+
+/* The kernel shapes a plan was built with (SDP_OK or SDP_ERR_INVALID_ARG). */
+int sdp_plan_tuning(sdp_plan_t plan, sdp_tuning* out);
+
 /* Release every resource of the plan (NULL is a no-op).  Synchronises the device. */
 void sdp_plan_destroy(sdp_plan_t plan);
 

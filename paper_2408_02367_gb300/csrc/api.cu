@@ -42,6 +42,7 @@ struct sdp_plan_s {
     FftAxis ax[3]{};
     int bs[3] = {0, 0, 0};
     int nb[3] = {0, 0, 0};
+    int spread_chunk = 0;
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -164,7 +165,7 @@ float grid_coord(float omega, long long M) {
     return g32;
 }
 
-int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
+int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cudaStream_t st) {
     const int W = d->width;
     const int K = d->K;
     const long long J = d->J;
@@ -195,8 +196,10 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     g.beta = (float)p->beta;
     g.inv_i0_beta = (float)(1.0 / i0(p->beta));
     g.halfW = (float)(0.5 * W);
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
         if (!fft_factor(g.M[a], &p->ax[a])) return SDP_ERR_UNSUPPORTED;
+        p->ax[a].generic = tn ? tn->fft_engine : 0;
+    }
 
     // ---- host tables ----
     std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
@@ -233,6 +236,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     // ---- bins: 8 x 4 x 8 grid points (one warp of the spread, a lane per axis-3
     // column of 8 points held in registers) ----
     int bs[3] = {8, 4, 8};
+    if (tn)
+        for (int a = 0; a < 3; ++a) bs[a] = tn->spread_bins[a];
     for (int a = 0; a < 3; ++a) {
         p->bs[a] = bs[a];
         p->nb[a] = (int)((p->M[a] + bs[a] - 1) / bs[a]);
@@ -329,7 +334,11 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, cudaStream_t st) {
     }
     // subproblems: every bin (empty ones too, they write zeros), chunks of at most kChunk
     long long kChunk = 512;
-    if (const char* ev = std::getenv("SDP_SPREAD_CHUNK")) kChunk = std::max(32LL, std::atoll(ev));
+    if (tn)
+        kChunk = tn->spread_chunk;
+    else if (const char* ev = std::getenv("SDP_SPREAD_CHUNK"))
+        kChunk = std::max(32LL, std::atoll(ev));
+    p->spread_chunk = (int)kChunk;
     std::vector<SubProb> subs;
     long long slots = 0;
     for (long long b = 0; b < nbins; ++b) {
@@ -598,8 +607,18 @@ int sdp_adjoint_batched(const sdp_work* items, int32_t n, void* stream) {
 }
 
 int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* d, void* stream) {
+    return sdp_plan_create_tuned(out, d, nullptr, stream);
+}
+
+int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tuning* tn, void* stream) {
     if (!out) return SDP_ERR_INVALID_ARG;
     *out = nullptr;
+    if (tn) {
+        if (tn->spread_chunk < 32 || tn->spread_chunk > 65536 || tn->fft_engine < 0 || tn->fft_engine > 1 ||
+            tn->reserved[0] || tn->reserved[1] || tn->reserved[2])
+            return SDP_ERR_INVALID_ARG;
+        if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
+    }
     if (!d || !d->traj || !d->V || !d->coil_maps || !d->frame_offsets) return SDP_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (d->n[a] < 2) return SDP_ERR_INVALID_ARG;
@@ -618,7 +637,7 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* d, void* stream) {
         delete p;
         return SDP_ERR_CUDA;
     }
-    const int rc = build_plan(p, d, static_cast<cudaStream_t>(stream));
+    const int rc = build_plan(p, d, tn, static_cast<cudaStream_t>(stream));
     if (rc != SDP_OK) {
         free_plan(p);
         return rc;
@@ -734,6 +753,15 @@ int sdp_plan_info(sdp_plan_t p, int64_t* out, int32_t cap) {
                            p->bs[2],       p->nbins,    p->nsub,   p->ninc,
                            (int64_t)p->workspace_bytes, (int64_t)p->total_bytes, p->geo.W, p->geo.C};
     for (int i = 0; i < cap && i < 16; ++i) out[i] = v[i];
+    return SDP_OK;
+}
+
+int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
+    if (!p || !out) return SDP_ERR_INVALID_ARG;
+    *out = sdp_tuning{};
+    for (int a = 0; a < 3; ++a) out->spread_bins[a] = p->bs[a];
+    out->spread_chunk = p->spread_chunk;
+    out->fft_engine = p->ax[0].generic;
     return SDP_OK;
 }
 

@@ -372,7 +372,7 @@ std::vector<float2> fft_twiddles(int L) {
 cudaError_t launch_fft_strided(const FftAxis& ax, int inverse, const float2* in, float2* out, int n_in,
                                int in_centred, int n_out, int out_centred, long long inner, long long outer,
                                cudaStream_t st) {
-    if (fft2_supported(ax.L) && !g_generic_only)
+    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic)
         return launch_fft2_strided(ax, inverse, in, out, n_in, in_centred, n_out, out_centred, inner, outer, st);
     const size_t sm = smem_fft_bytes(ax.L);
     const long long ncolblk = (inner + NL - 1) / NL;
@@ -396,7 +396,7 @@ cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int* status,
                                      cudaStream_t st) {
-    if (fft2_supported(ax.L) && !g_generic_only)
+    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic)
         return launch_fft2_fwd_prologue(g, ax, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, status, st);
     const size_t sm = smem_fft_bytes(ax.L);
     const long long nlines = (long long)g.N[0] * g.N[1] * nk;
@@ -412,7 +412,7 @@ cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int accumulate,
                                      int* status, cudaStream_t st) {
-    if (fft2_supported(ax.L) && !g_generic_only)
+    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic)
         return launch_fft2_adj_epilogue(g, ax, in, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, accumulate,
                                         status, st);
     const size_t sm = smem_fft_bytes(ax.L) + (size_t)g.N[2] * NLP * sizeof(float2);

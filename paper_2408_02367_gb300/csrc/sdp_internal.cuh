@@ -37,6 +37,7 @@ struct FftAxis {
     int nst;
     int radix[kMaxRadixStages];
     const float2* tw;
+    int generic;   // 1: always the Stockham kernels (a plan's tuning), 0: two-pass where available
 };
 
 // A spread subproblem: one chunk of the incidence list of one output bin.
@@ -68,6 +69,8 @@ struct Geo {
 inline int channel_group(int nk) { return nk <= 5 ? nk : 8; }
 
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
+// Spread bin shapes with a kernel: 8 x 4 x 8 and 8 x 4 x 4 grid points.
+bool spread_bins_supported(const int bs[3]);
 cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int* status,

@@ -1,324 +1,26 @@
-// Adjoint spreading with the conjugate subspace weights (gridding step A5):
-//
-//   H_{b,k}[m mod M] = sum_j phi(g_j1 - m1) phi(g_j2 - m2) phi(g_j3 - m3) conj(V[t_j, k]) r_b[j]
-//
-// the first step of A_c^H, which Algorithm 1 of StoDIP needs for
-// loss.backward() (Sec. 2.1, Eq. 3).  conj(V[t_j, k]) r_b[j] folds the
-// temporal subspace into the spread, so only K channel grids are formed.
-//
-// Owner-computes bins.  The grid is cut into bins of 8 x 4 x 8 points.  The
-// plan lists, per bin, every sample whose W^3 window touches the bin (the
-// incidences), split into chunks of bounded length (the subproblems).  A CTA
-// is ONE warp that takes one subproblem for one coil b; lane l owns the
-// axis-3 column (l / 4, l % 4) of the bin and accumulates its 8 points x the
-// channels of the call in registers:
-//   - incidences are staged 32 at a time (window start, the 3W plan-time
-//     Kaiser-Bessel weights, c_k = conj(V[t, k]) r) in shared memory;
-//   - for each incidence a lane multiplies its two axis-1/axis-2 weights and
-//     adds w phi3 c_k into the axis-3 positions the window covers;
-//   - single-chunk bin: the columns are stored straight into the grid;
-//     multi-chunk bin (the dense k-space centre): each chunk stores a partial
-//     tile and the last chunk to finish (device-scope counter, no waiting)
-//     sums the partials in chunk order and stores the bin.
-// Every grid point is written exactly once by plain 16-byte stores: no zero
-// fill of the grid, no atomics on it and no shared-memory accumulation.
-#include "sdp_internal.cuh"
+// Adjoint spreading, bins of 8 x 4 x 8 grid points, and the bin-shape dispatch
+// of launch_spread (the kernel itself is in spread_impl.cuh; spread_b4.cu
+// instantiates the 8 x 4 x 4 bins in a translation unit of its own).
+#include "spread_impl.cuh"
 
 namespace sdp {
-namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+cudaError_t launch_spread_b4(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
+                             const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
+                             const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
+                             float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
 
-__device__ __forceinline__ int wrap1(int i, int M) { return i < 0 ? i + M : (i >= M ? i - M : i); }
-
-struct SpreadArgs {
-    Geo g;
-    int bs1, bs2, bs3;
-    int nb1, nb2, nb3;
-    const SubProb* subs;
-    const int* inc;
-    const float4* pts;
-    const int* tframe;
-    const float* wts;
-    const float2* V;
-    const float2* y;
-    const float* scale;
-    int k0, nk;
-    float2* grids;
-    float2* partials;
-    long long slots_per_b;
-    long long slot_elems;
-    int* counters;
-    int nbins;
-    int ngroups;   // channel groups of this call (counters are per group)
-    int group;
-};
-
-// Bins are 8 x 4 x 8 grid points (axis 1 x axis 2 x axis 3).  Lane l of the
-// warp owns the axis-3 column (x1, x2) = (l / 4, l % 4) of the bin: its 8
-// points x NK channels are accumulated in REGISTERS, so there is no shared
-// tile, no load-add-store chain and no bank conflict.  Per incidence a lane
-// forms w12 = phi1(x1) phi2(x2) (zero outside the window) and then, for the
-// axis-3 positions the window covers (a warp-uniform test), adds
-// w12 phi3(x3) conj(V[t, k]) r into acc[x3][k].
-constexpr int B1 = 8, B2 = 4, B3 = 8;
-constexpr int BP = B1 * B2 * B3;
-
-// Two packed (Re, Im) accumulators as one float4 (Re0, Im0, Re1, Im1).
-__device__ __forceinline__ float4 pair4(unsigned long long a, unsigned long long b) {
-    float4 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.z), "=f"(r.w) : "l"(b));
-    return r;
-}
-
-template <int W, int NK>
-__global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
-    constexpr int NW = 3 * W;
-    constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
-    __shared__ float psm[32 * NP];            // [incidence][x1 (8) | x2 (4)], 0 outside the window
-    __shared__ float2 p3sm[32 * B3];          // [incidence][x3]: (w3, w3), 0 outside the window
-    __shared__ unsigned msm[32];              // axis-3 positions the window covers (bit x3)
-    __shared__ float2 csm[32 * NK];
-    const Geo& g = a.g;
-    const int lane = threadIdx.x;
-    const int x1 = lane >> 2, x2 = lane & 3;
-    const SubProb sp = a.subs[blockIdx.x];
-    const int b = blockIdx.y;
-    const int bin3 = sp.bin % a.nb3;
-    const int bt = sp.bin / a.nb3;
-    const int bin2 = bt % a.nb2;
-    const int bin1 = bt / a.nb2;
-    const int lo1 = bin1 * B1, lo2 = bin2 * B2, lo3 = bin3 * B3;
-    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
-    const long long G = (long long)M1 * M2 * M3;
-
-    // accumulators as packed (Re, Im) pairs for the f32x2 multiply-adds
-    unsigned long long acc[B3][NK];
-#pragma unroll
-    for (int x3 = 0; x3 < B3; ++x3)
-#pragma unroll
-        for (int q = 0; q < NK; ++q) acc[x3][q] = 0ull;
-
-    const float2* yb = a.y + (long long)b * g.J;
-    const float sc = a.scale ? __ldg(a.scale) : 1.f;
-    const int kv = a.k0 + kofs;   // first channel of V of this group
-    for (int base = 0; base < sp.count; base += 32) {
-        const int n = min(32, sp.count - base);
-        if (lane < n) {
-            const int s = __ldg(a.inc + sp.start + base + lane);
-            const float4 p = __ldg(a.pts + s);
-            const int orig = __float_as_int(p.w);
-            const int t = __ldg(a.tframe + s);
-            float2 r = __ldg(yb + orig);
-            r.x *= sc;
-            r.y *= sc;
-            const float* ws = a.wts + (long long)s * NW;
-            float wl[NW];
-#pragma unroll
-            for (int q = 0; q < NW; ++q) wl[q] = __ldg(ws + q);
-            // tap offset of every bin position, wrapped onto the periodic grid:
-            // position x takes weight phi_d(a) with a = (lo + x - m0) mod M if a < W
-            const int m01 = (int)ceilf(p.x - g.halfW), m02 = (int)ceilf(p.y - g.halfW);
-            const int m03 = (int)ceilf(p.z - g.halfW);
-            float* pw = psm + lane * NP;
-#pragma unroll
-            for (int x = 0; x < B1; ++x) {
-                int aa = lo1 + x - m01;
-                aa += aa < 0 ? M1 : 0;
-                aa -= aa >= M1 ? M1 : 0;
-                float v = 0.f;
-#pragma unroll
-                for (int q = 0; q < W; ++q) v = aa == q ? wl[q] : v;
-                pw[x] = v;
-            }
-#pragma unroll
-            for (int x = 0; x < B2; ++x) {
-                int aa = lo2 + x - m02;
-                aa += aa < 0 ? M2 : 0;
-                aa -= aa >= M2 ? M2 : 0;
-                float v = 0.f;
-#pragma unroll
-                for (int q = 0; q < W; ++q) v = aa == q ? wl[W + q] : v;
-                pw[B1 + x] = v;
-            }
-            unsigned mask = 0;
-#pragma unroll
-            for (int x = 0; x < B3; ++x) {
-                int aa = lo3 + x - m03;
-                aa += aa < 0 ? M3 : 0;
-                aa -= aa >= M3 ? M3 : 0;
-                float v = 0.f;
-#pragma unroll
-                for (int q = 0; q < W; ++q) v = aa == q ? wl[2 * W + q] : v;
-                p3sm[lane * B3 + x] = make_float2(v, v);
-                mask |= ((unsigned)aa < (unsigned)W ? 1u : 0u) << x;
-            }
-            msm[lane] = mask;
-            const float2* Vt = a.V + (long long)t * g.K + kv;
-#pragma unroll
-            for (int q = 0; q < NK; ++q) {
-                const float2 v = __ldg(Vt + q);
-                csm[lane * NK + q] = make_float2(v.x * r.x + v.y * r.y, v.x * r.y - v.y * r.x);
-            }
-        }
-        __syncwarp();
-        for (int i = 0; i < n; ++i) {
-            const float* pw = psm + i * NP;
-            const unsigned mask = msm[i];
-            const float w12 = pw[x1] * pw[B1 + x2];
-            unsigned long long w12p;
-            asm("mov.b64 %0, {%1, %1};" : "=l"(w12p) : "f"(w12));
-            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(csm + i * NK);
-            const unsigned long long* wp3 = reinterpret_cast<const unsigned long long*>(p3sm + i * B3);
-            unsigned long long c[NK];
-#pragma unroll
-            for (int q = 0; q < NK; ++q) c[q] = cp[q];
-#pragma unroll
-            for (int x3 = 0; x3 < B3; ++x3) {
-                if (mask & (1u << x3)) {                 // the same for every lane
-                    // w = w12 * w3 and acc += w * c, both components at once (round to nearest
-                    // per component: the same arithmetic as two scalar multiplies and FMAs)
-                    unsigned long long w;
-                    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(w) : "l"(w12p), "l"(wp3[x3]));
-#pragma unroll
-                    for (int q = 0; q < NK; ++q) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[x3][q]) : "l"(w), "l"(c[q]));
-                }
-            }
-        }
-        __syncwarp();
-    }
-
-    // store: this lane's column, two points per 16-byte store (M3, lo3 even)
-    const int j1 = lo1 + x1, j2 = lo2 + x2;
-    float2* gcol = a.grids + ((long long)b * a.nk + kofs) * G + ((long long)j1 * M2 + j2) * M3 + lo3;
-    const bool colok = j1 < M1 && j2 < M2;
-    if (sp.nchunks == 1) {
-        if (colok) {
-#pragma unroll
-            for (int q = 0; q < NK; ++q)
-#pragma unroll
-                for (int x3 = 0; x3 < B3; x3 += 2)
-                    if (lo3 + x3 < M3)
-                        *reinterpret_cast<float4*>(gcol + q * G + x3) =
-                            pair4(acc[x3][q], acc[x3 + 1][q]);
-        }
-        return;
-    }
-    // multi-chunk bin: partial columns [q][lane][x3] in the chunk's slot; the last chunk sums them
-    float4* part = reinterpret_cast<float4*>(a.partials +
-                                             ((long long)b * a.slots_per_b + sp.slot + sp.chunk) * a.slot_elems +
-                                             (long long)kofs * BP);
-#pragma unroll
-    for (int q = 0; q < NK; ++q)
-#pragma unroll
-        for (int x3 = 0; x3 < B3; x3 += 2)
-            part[(q * BP + lane * B3 + x3) / 2] =
-                pair4(acc[x3][q], acc[x3 + 1][q]);
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0)
-        last = (atomicAdd(a.counters + ((long long)b * a.ngroups + a.group) * a.nbins + sp.bin, 1) ==
-                sp.nchunks - 1);
-    last = __shfl_sync(kFull, last, 0);
-    if (!last) return;
-    __threadfence();
-    const float2* part0 =
-        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP;
-#pragma unroll
-    for (int q = 0; q < NK; ++q) {
-#pragma unroll
-        for (int x3 = 0; x3 < B3; x3 += 2) {
-            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int ch = 0; ch < sp.nchunks; ++ch) {
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(part0 + ch * a.slot_elems) +
-                                        (q * BP + lane * B3 + x3) / 2);
-                sum.x += v.x;
-                sum.y += v.y;
-                sum.z += v.z;
-                sum.w += v.w;
-            }
-            if (colok && lo3 + x3 < M3) *reinterpret_cast<float4*>(gcol + q * G + x3) = sum;
-        }
-    }
-    if (lane == 0) a.counters[((long long)b * a.ngroups + a.group) * a.nbins + sp.bin] = 0;
-}
-
-template <int W, int NK>
-cudaError_t launch_wk(const SpreadArgs& a, int kofs, int nsub, int B, cudaStream_t st) {
-    dim3 grid((unsigned)nsub, (unsigned)B);
-    spread_kernel<W, NK><<<grid, 32, 0, st>>>(a, kofs);
-    return cudaGetLastError();
-}
-
-// Channels run in groups of at most 8 (one launch each, exact group size).
-template <int W>
-cudaError_t launch_w(SpreadArgs a, int nsub, int B, cudaStream_t st) {
-    if (a.bs1 != B1 || a.bs2 != B2 || a.bs3 != B3) return cudaErrorInvalidValue;
-    a.ngroups = (a.nk + 7) / 8;
-    for (int gi = 0; gi < a.ngroups; ++gi) {
-        const int kofs = gi * 8;
-        const int ng = a.nk - kofs < 8 ? a.nk - kofs : 8;
-        a.group = gi;
-        cudaError_t e;
-        switch (ng) {
-            case 1: e = launch_wk<W, 1>(a, kofs, nsub, B, st); break;
-            case 2: e = launch_wk<W, 2>(a, kofs, nsub, B, st); break;
-            case 3: e = launch_wk<W, 3>(a, kofs, nsub, B, st); break;
-            case 4: e = launch_wk<W, 4>(a, kofs, nsub, B, st); break;
-            case 5: e = launch_wk<W, 5>(a, kofs, nsub, B, st); break;
-            case 6: e = launch_wk<W, 6>(a, kofs, nsub, B, st); break;
-            case 7: e = launch_wk<W, 7>(a, kofs, nsub, B, st); break;
-            default: e = launch_wk<W, 8>(a, kofs, nsub, B, st); break;
-        }
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-}  // namespace
+bool spread_bins_supported(const int bs[3]) { return bs[0] == 8 && bs[1] == 4 && (bs[2] == 8 || bs[2] == 4); }
 
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
                           const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
                           float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st) {
-    SpreadArgs a;
-    a.g = g;
-    a.bs1 = bs[0];
-    a.bs2 = bs[1];
-    a.bs3 = bs[2];
-    a.nb1 = nb[0];
-    a.nb2 = nb[1];
-    a.nb3 = nb[2];
-    a.subs = subs;
-    a.inc = inc;
-    a.pts = pts;
-    a.tframe = tframe;
-    a.wts = wts;
-    a.V = V;
-    a.y = y;
-    a.scale = scale;
-    a.k0 = k0;
-    a.nk = nk;
-    a.grids = grids;
-    a.partials = partials;
-    a.slots_per_b = slots_per_b;
-    a.slot_elems = (long long)g.K * bs[0] * bs[1] * bs[2];
-    a.counters = counters;
-    a.nbins = nbins;
-    a.ngroups = 1;
-    a.group = 0;
-    switch (g.W) {
-        case 2: return launch_w<2>(a, nsub, B, st);
-        case 3: return launch_w<3>(a, nsub, B, st);
-        case 4: return launch_w<4>(a, nsub, B, st);
-        case 5: return launch_w<5>(a, nsub, B, st);
-        case 6: return launch_w<6>(a, nsub, B, st);
-        case 7: return launch_w<7>(a, nsub, B, st);
-        case 8: return launch_w<8>(a, nsub, B, st);
-        default: return cudaErrorInvalidValue;
-    }
+    if (bs[2] == 4)
+        return launch_spread_b4(g, bs, nb, subs, nsub, inc, pts, tframe, wts, V, y, scale, B, k0, nk, grids, partials,
+                                slots_per_b, counters, nbins, st);
+    return launch_spread_depth<8>(g, bs, nb, subs, nsub, inc, pts, tframe, wts, V, y, scale, B, k0, nk, grids,
+                                  partials, slots_per_b, counters, nbins, st);
 }
 
 }  // namespace sdp

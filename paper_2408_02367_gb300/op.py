@@ -52,6 +52,29 @@ class PlanDesc(ctypes.Structure):
     ]
 
 
+class Tuning(ctypes.Structure):
+    """sdp_tuning: kernel shapes of a plan (include/stodip_op.h)."""
+    _fields_ = [
+        ("spread_bins", ctypes.c_int32 * 3),
+        ("spread_chunk", ctypes.c_int32),
+        ("fft_engine", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+    @staticmethod
+    def of(d):
+        """From a dict {spread_bins: (8, 4, 8), spread_chunk: 512, fft_engine: 0}."""
+        t = Tuning()
+        t.spread_bins = (ctypes.c_int32 * 3)(*[int(v) for v in d.get("spread_bins", (8, 4, 8))])
+        t.spread_chunk = int(d.get("spread_chunk", 512))
+        t.fft_engine = int(d.get("fft_engine", 0))
+        return t
+
+    def as_dict(self):
+        return {"spread_bins": tuple(int(v) for v in self.spread_bins), "spread_chunk": int(self.spread_chunk),
+                "fft_engine": int(self.fft_engine)}
+
+
 class Work(ctypes.Structure):
     _fields_ = [
         ("plan", ctypes.c_void_p),
@@ -68,6 +91,9 @@ _LIB = None
 EXPORTS = {
     "sdp_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc), ctypes.c_void_p]),
     "sdp_plan_destroy": (None, [ctypes.c_void_p]),
+    "sdp_plan_create_tuned": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc),
+                                             ctypes.POINTER(Tuning), ctypes.c_void_p]),
+    "sdp_plan_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Tuning)]),
     "sdp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p]),
     "sdp_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
@@ -175,7 +201,7 @@ class SubspaceNufft:
     V         complex64 [T][K] (device), coil_maps complex64 [C][N1][N2][N3] (device).
     """
 
-    def __init__(self, traj, frame_offsets, n, width, oversamp, V, coil_maps, max_batch=1):
+    def __init__(self, traj, frame_offsets, n, width, oversamp, V, coil_maps, max_batch=1, tuning=None):
         if not torch.cuda.is_available():
             raise RuntimeError("SubspaceNufft needs a CUDA device (no CPU fallback)")
         self.device = traj.device
@@ -206,12 +232,21 @@ class SubspaceNufft:
         d.coil_maps = coil_maps.data_ptr()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(L.sdp_plan_create(ctypes.byref(h), ctypes.byref(d), _stream_ptr(self.device)), "sdp_plan_create")
+            if tuning is None:
+                _check(L.sdp_plan_create(ctypes.byref(h), ctypes.byref(d), _stream_ptr(self.device)),
+                       "sdp_plan_create")
+            else:
+                t = Tuning.of(tuning)
+                _check(L.sdp_plan_create_tuned(ctypes.byref(h), ctypes.byref(d), ctypes.byref(t),
+                                               _stream_ptr(self.device)), "sdp_plan_create_tuned")
         self._h = h
         self.K, self.T, self.C, self.J = int(K), int(T), int(C), int(J)
         self.max_batch = int(max_batch)
         self.width = int(width)
         self.oversamp = float(oversamp)
+        t = Tuning()
+        _check(L.sdp_plan_tuning(self._h, ctypes.byref(t)), "sdp_plan_tuning")
+        self.tuning = t.as_dict()
 
     # -- lifetime --
     def close(self):
@@ -501,7 +536,7 @@ def tv_loss(op: SubspaceNufft, x, lam: float, eps: float = 1e-6):
     return _TotalVariation.apply(x, op, float(lam), float(eps))
 
 
-def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda"):
+def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda", tuning=None):
     """Plan from numpy inputs (omega float32 [J][3], frame int [J] non-decreasing)."""
     T = V.shape[0]
     off = np.searchsorted(np.asarray(frame), np.arange(T + 1), side="left").astype(np.int64)
@@ -509,4 +544,5 @@ def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cud
     dev = torch.device(device)
     return SubspaceNufft(torch.from_numpy(np.ascontiguousarray(omega, np.float32)).to(dev), off, n, width,
                          oversamp, torch.from_numpy(np.ascontiguousarray(V, np.complex64)).to(dev),
-                         torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev), max_batch=max_batch)
+                         torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev), max_batch=max_batch,
+                         tuning=tuning)

@@ -88,3 +88,21 @@ def test_dictionary_matcher_rejects_bad_arguments_on_the_host(lib):
     buf = (ctypes.c_int64 * 8)()
     assert lib.sdp_dm_info(None, buf, 8) == 1
     lib.sdp_dm_destroy(None)
+
+
+def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
+    from paper_2408_02367_gb300 import op
+    h = ctypes.c_void_p(1234)
+    t = op.Tuning.of({"spread_bins": (8, 4, 8), "spread_chunk": 16})          # chunk below 32
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    assert h.value is None
+    t = op.Tuning.of({"spread_bins": (8, 8, 8)})                               # no kernel for this shape
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 6
+    t = op.Tuning.of({"fft_engine": 2})
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({})
+    t.reserved[1] = 3
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({})                                                       # valid tuning, no descriptor
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    assert lib.sdp_plan_tuning(None, ctypes.byref(t)) == 1

@@ -133,6 +133,42 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
 
 
+@pytest.mark.parametrize("tuning", [
+    {"spread_bins": (8, 4, 4), "spread_chunk": 64, "fft_engine": 0},
+    {"spread_bins": (8, 4, 8), "spread_chunk": 32, "fft_engine": 1},
+])
+def test_tuned_kernel_shapes_match_oracle(tuning):
+    """Every tuning computes the same operator: half-depth spread bins, short spread
+    chunks (many multi-chunk bins) and the Stockham FFT engine, forward and adjoint."""
+    from paper_2408_02367_gb300 import op
+    c = make_case((20, 18, 16), 4, 1.25, 3, 3, 10, 1, 600, [2, 0])
+    geo = O.Geometry(c["n"], 4, 1.25)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2, tuning=tuning)
+    assert A.tuning["spread_bins"] == tuple(tuning["spread_bins"]) and A.tuning["spread_chunk"] == tuning["spread_chunk"]
+    y = A.forward(t(c["x"]), t(c["coils"])).cpu().numpy()
+    assert rel(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"])) < FP32_BOUND
+    r = np.ascontiguousarray(y)
+    a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
+    assert rel(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"])) < FP32_BOUND
+    assert A.status() == 0
+
+
+def test_autotuner_candidates_agree_and_cache(tmp_path):
+    from paper_2408_02367_gb300 import tune
+    c = make_case((24, 20, 16), 4, 1.25, 3, 3, 10, 1, 600, [0, 1])
+    cands = tune.candidates()[:2] + tune.candidates()[3:5] + tune.candidates()[-1:]
+    cache = str(tmp_path / "tune.json")
+    best, table = tune.autotune(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2, cands=cands,
+                                reps=3, cache=cache)
+    assert len(table) == len(cands)
+    assert [r["ms"] for r in table] == sorted(r["ms"] for r in table)
+    assert all(r["rel_vs_first"] <= 1e-5 for r in table)
+    assert best["spread_bins"] == tuple(table[0]["tuning"]["spread_bins"])
+    best2, table2 = tune.autotune(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2,
+                                  cands=cands, reps=3, cache=cache)
+    assert best2 == best and table2 == table                     # served from the cache
+
+
 def test_adjoint_identity_on_gpu():
     c = make_case((24, 20, 28), 4, 1.25, 5, 4, 30, 1, 400, [3, 1, 2])
     A = gpu_op(c)
