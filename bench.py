@@ -566,10 +566,32 @@ def run_native(args):
         bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
     del matcher, xd, dm_out
 
+    # the full stochastic DIP iteration of Algorithm 1 with the 4-level 3D U-Net generator and Adam
+    from paper_2408_02367_gb300 import dip
+    torch.backends.cudnn.benchmark = True
+    torch.manual_seed(0)
+    net = dip.UNet3D(2 * w.K, 2 * w.K).to(dev)
+    z = torch.rand((1, 2 * w.K) + tuple(w.n), generator=torch.Generator().manual_seed(1)).mul_(0.1).to(dev)
+    runner = dip.DipRunner(A, y_meas, net, z, B=B, lr=1e-3)
+    for _ in range(3):
+        runner.step()
+    torch.cuda.synchronize()
+    un_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a_ev, b_ev in un_ev:
+        a_ev.record()
+        runner.step()
+        b_ev.record()
+    torch.cuda.synchronize()
+    unet_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in un_ev)[len(un_ev) // 2]
+    del runner, net, z
+
     rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
             "tv_value_ms": tv_val_ms, "tv_value_gbs": xb / (tv_val_ms * 1e-3) / 1e9,
             "tv_grad_ms": tv_grad_ms, "tv_grad_gbs": 2 * xb / (tv_grad_ms * 1e-3) / 1e9,
             "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
+            "dip_unet_step_ms": unet_ms,
+            "dip_unet_note": "G(z) by a 4-level 3D U-Net (32..256 channels, cuDNN, TF32 convolutions allowed), "
+                             "DC loss of a coil minibatch through the library, backward, Adam; median of 5",
             "dm_ms": dm_ms, "dm_atoms": int(Dm.shape[0]), "dm_voxels": int(w.nvox),
             "dm_gpairs_per_s": w.nvox * Dm.shape[0] / (dm_ms * 1e-3) / 1e9,
             "dm_tensor_tflops": dm_tflops, "dm_tensor_frac_of_measured_bf16": dm_tflops / bf16_peak,
