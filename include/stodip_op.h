@@ -116,13 +116,18 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 bounds the work of one CTA on the dense k-space centre.
  *   fft_engine    0: two-pass register FFTs where the length has one (default),
  *                 1: the radix-2/3/4/5 Stockham kernels for every length.
+ *   fft_lines     grid lines per CTA of the fused axis-3 FFT kernels (the
+ *                 forward prologue and the adjoint epilogue): 0 (default: 16,
+ *                 or 8 for lengths >= 240), 8 or 4 (fewer lines: more, smaller
+ *                 CTAs, so more of them resident per SM).
  *   reserved      must be 0.
  */
 typedef struct {
     int32_t spread_bins[3];
     int32_t spread_chunk;
     int32_t fft_engine;
-    int32_t reserved[3];
+    int32_t fft_lines;
+    int32_t reserved[2];
 } sdp_tuning;
 
 /*

@@ -199,6 +199,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     for (int a = 0; a < 3; ++a) {
         if (!fft_factor(g.M[a], &p->ax[a])) return SDP_ERR_UNSUPPORTED;
         p->ax[a].generic = tn ? tn->fft_engine : 0;
+        p->ax[a].lines = tn ? tn->fft_lines : 0;
     }
 
     // ---- host tables ----
@@ -615,7 +616,7 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
     *out = nullptr;
     if (tn) {
         if (tn->spread_chunk < 32 || tn->spread_chunk > 65536 || tn->fft_engine < 0 || tn->fft_engine > 1 ||
-            tn->reserved[0] || tn->reserved[1] || tn->reserved[2])
+            (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) || tn->reserved[0] || tn->reserved[1])
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -762,6 +763,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     for (int a = 0; a < 3; ++a) out->spread_bins[a] = p->bs[a];
     out->spread_chunk = p->spread_chunk;
     out->fft_engine = p->ax[0].generic;
+    out->fft_lines = p->ax[2].lines;
     return SDP_OK;
 }
 

@@ -493,6 +493,52 @@ bool with_shape(int L, F&& f) {
     }
 }
 
+// The same shapes with 8 lines per CTA (a plan's tuning, for the fused axis-3 kernels).
+template <class F>
+bool with_shape8(int L, F&& f) {
+    switch (L) {
+        case 48: f(Shape<8, 6, 8>{}); return true;
+        case 64: f(Shape<8, 8, 8>{}); return true;
+        case 80: f(Shape<10, 8, 8>{}); return true;
+        case 96: f(Shape<12, 8, 8>{}); return true;
+        case 100: f(Shape<10, 10, 8>{}); return true;
+        case 120: f(Shape<12, 10, 8>{}); return true;
+        case 128: f(Shape<16, 8, 8>{}); return true;
+        case 160: f(Shape<16, 10, 8>{}); return true;
+        case 200: f(Shape<20, 10, 8>{}); return true;
+        case 240: f(Shape<16, 15, 8>{}); return true;
+        case 250: f(Shape<25, 10, 8>{}); return true;
+        case 256: f(Shape<16, 16, 8>{}); return true;
+        default: return false;
+    }
+}
+
+// ... and with 4 lines per CTA.
+template <class F>
+bool with_shape4(int L, F&& f) {
+    switch (L) {
+        case 48: f(Shape<8, 6, 4>{}); return true;
+        case 64: f(Shape<8, 8, 4>{}); return true;
+        case 80: f(Shape<10, 8, 4>{}); return true;
+        case 96: f(Shape<12, 8, 4>{}); return true;
+        case 100: f(Shape<10, 10, 4>{}); return true;
+        case 120: f(Shape<12, 10, 4>{}); return true;
+        case 128: f(Shape<16, 8, 4>{}); return true;
+        case 160: f(Shape<16, 10, 4>{}); return true;
+        case 200: f(Shape<20, 10, 4>{}); return true;
+        case 240: f(Shape<16, 15, 4>{}); return true;
+        case 250: f(Shape<25, 10, 4>{}); return true;
+        case 256: f(Shape<16, 16, 4>{}); return true;
+        default: return false;
+    }
+}
+
+template <class F>
+bool with_shape_of(const FftAxis& ax, F&& f) {
+    if (ax.lines == 4) return with_shape4(ax.L, f);
+    return ax.lines == 8 ? with_shape8(ax.L, f) : with_shape(ax.L, f);
+}
+
 }  // namespace
 
 bool fft2_supported(int L) {
@@ -532,7 +578,7 @@ cudaError_t launch_fft2_fwd_prologue(const Geo& g, const FftAxis& ax, const floa
                                      cudaStream_t st) {
     const long long nlines = (long long)g.N[0] * g.N[1] * nk;
     cudaError_t err = cudaErrorNotSupported;
-    with_shape(ax.L, [&](auto sh) {
+    with_shape_of(ax, [&](auto sh) {
         using Sh = decltype(sh);
         const long long nblk = (nlines + Sh::nl - 1) / Sh::nl * B;
         if (nblk > 0x7fffffffLL) {
@@ -552,7 +598,7 @@ cudaError_t launch_fft2_adj_epilogue(const Geo& g, const FftAxis& ax, const floa
                                      int* status, cudaStream_t st) {
     const long long nlines = (long long)g.N[0] * g.N[1] * nk;
     cudaError_t err = cudaErrorNotSupported;
-    with_shape(ax.L, [&](auto sh) {
+    with_shape_of(ax, [&](auto sh) {
         using Sh = decltype(sh);
         const long long nblk = (nlines + Sh::nl - 1) / Sh::nl;
         fft2_adj_epilogue_kernel<Sh::a, Sh::b, Sh::nl><<<(unsigned)nblk, Sh::threads, 0, st>>>(

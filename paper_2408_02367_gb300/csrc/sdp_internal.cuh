@@ -38,6 +38,7 @@ struct FftAxis {
     int radix[kMaxRadixStages];
     const float2* tw;
     int generic;   // 1: always the Stockham kernels (a plan's tuning), 0: two-pass where available
+    int lines;     // lines per CTA of the fused axis-3 kernels: 0 = default, 8 or 4
 };
 
 // A spread subproblem: one chunk of the incidence list of one output bin.

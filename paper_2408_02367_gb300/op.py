@@ -58,21 +58,23 @@ class Tuning(ctypes.Structure):
         ("spread_bins", ctypes.c_int32 * 3),
         ("spread_chunk", ctypes.c_int32),
         ("fft_engine", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("fft_lines", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
     @staticmethod
     def of(d):
-        """From a dict {spread_bins: (8, 4, 8), spread_chunk: 512, fft_engine: 0}."""
+        """From a dict {spread_bins: (8, 4, 8), spread_chunk: 512, fft_engine: 0, fft_lines: 0}."""
         t = Tuning()
         t.spread_bins = (ctypes.c_int32 * 3)(*[int(v) for v in d.get("spread_bins", (8, 4, 8))])
         t.spread_chunk = int(d.get("spread_chunk", 512))
         t.fft_engine = int(d.get("fft_engine", 0))
+        t.fft_lines = int(d.get("fft_lines", 0))
         return t
 
     def as_dict(self):
         return {"spread_bins": tuple(int(v) for v in self.spread_bins), "spread_chunk": int(self.spread_chunk),
-                "fft_engine": int(self.fft_engine)}
+                "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines)}
 
 
 class Work(ctypes.Structure):

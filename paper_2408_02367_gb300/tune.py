@@ -8,7 +8,8 @@ the operator computes, only how fast it runs on a given trajectory and volume:
   about 1.3x the (sample, bin) incidences of a W = 4 window);
 - spread chunk length: incidences per spread CTA (load balance on the dense
   k-space centre against the cost of summing partial tiles);
-- FFT engine: the two-pass register FFTs or the Stockham kernels.
+- FFT engine: the two-pass register FFTs or the Stockham kernels;
+- FFT lines per CTA of the fused axis-3 prologue and epilogue (16, 8 or 4).
 
 `autotune` builds a plan for every candidate on the caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
@@ -29,18 +30,22 @@ import torch
 
 from . import op as _op
 
-DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0}
+DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0}
 
 
 def candidates(full: bool = False):
     """The tunings tried: both bin depths x three chunk lengths with the two-pass
-    FFTs, and the Stockham engine on the default spread; `full` adds more chunks."""
+    FFTs, both bin depths with 8 and 4 FFT lines per CTA, and the Stockham engine on
+    the default spread; `full` adds more chunks."""
     chunks = (128, 256, 512, 1024, 2048) if full else (256, 512, 1024)
     out = []
     for bins in ((8, 4, 8), (8, 4, 4)):
         for c in chunks:
-            out.append({"spread_bins": bins, "spread_chunk": c, "fft_engine": 0})
-    out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1})
+            out.append({"spread_bins": bins, "spread_chunk": c, "fft_engine": 0, "fft_lines": 0})
+    for bins in ((8, 4, 8), (8, 4, 4)):
+        for lines in (8, 4):
+            out.append({"spread_bins": bins, "spread_chunk": 512, "fft_engine": 0, "fft_lines": lines})
+    out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
     return out
 
 

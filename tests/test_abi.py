@@ -100,6 +100,8 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 6
     t = op.Tuning.of({"fft_engine": 2})
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"fft_lines": 12})                                       # 0, 8 or 4 only
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})
     t.reserved[1] = 3
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
