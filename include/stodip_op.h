@@ -120,6 +120,9 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 forward prologue and the adjoint epilogue): 0 (default: 16,
  *                 or 8 for lengths >= 240), 8 or 4 (fewer lines: more, smaller
  *                 CTAs, so more of them resident per SM).
+ *   fft_cols      grid columns per CTA of the strided axis-1 and axis-2 FFT
+ *                 passes: 0 (default: 16, or 8 for lengths >= 240), 32 (lengths
+ *                 up to 160; longer axes keep the default) or 8.
  *   reserved      must be 0.
  */
 typedef struct {
@@ -127,7 +130,8 @@ typedef struct {
     int32_t spread_chunk;
     int32_t fft_engine;
     int32_t fft_lines;
-    int32_t reserved[2];
+    int32_t fft_cols;
+    int32_t reserved[1];
 } sdp_tuning;
 
 /*

@@ -200,6 +200,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
         if (!fft_factor(g.M[a], &p->ax[a])) return SDP_ERR_UNSUPPORTED;
         p->ax[a].generic = tn ? tn->fft_engine : 0;
         p->ax[a].lines = tn ? tn->fft_lines : 0;
+        p->ax[a].cols = tn ? tn->fft_cols : 0;
     }
 
     // ---- host tables ----
@@ -616,7 +617,8 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
     *out = nullptr;
     if (tn) {
         if (tn->spread_chunk < 32 || tn->spread_chunk > 65536 || tn->fft_engine < 0 || tn->fft_engine > 1 ||
-            (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) || tn->reserved[0] || tn->reserved[1])
+            (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) ||
+            (tn->fft_cols != 0 && tn->fft_cols != 32 && tn->fft_cols != 8) || tn->reserved[0])
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -764,6 +766,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->spread_chunk = p->spread_chunk;
     out->fft_engine = p->ax[0].generic;
     out->fft_lines = p->ax[2].lines;
+    out->fft_cols = p->ax[0].cols;
     return SDP_OK;
 }
 

@@ -533,6 +533,32 @@ bool with_shape4(int L, F&& f) {
     }
 }
 
+// 32 columns per CTA for the strided passes (a plan's tuning); the shared staging
+// of L x 32 complex values stays within the 48 KB of static shared memory up to L = 160.
+template <class F>
+bool with_shape32(int L, F&& f) {
+    switch (L) {
+        case 48: f(Shape<8, 6, 32>{}); return true;
+        case 64: f(Shape<8, 8, 32>{}); return true;
+        case 80: f(Shape<10, 8, 32>{}); return true;
+        case 96: f(Shape<12, 8, 32>{}); return true;
+        case 100: f(Shape<10, 10, 32>{}); return true;
+        case 120: f(Shape<12, 10, 32>{}); return true;
+        case 128: f(Shape<16, 8, 32>{}); return true;
+        case 160: f(Shape<16, 10, 32>{}); return true;
+        default: return false;
+    }
+}
+
+
+// Strided passes: the column count of the plan's tuning where a kernel exists, else the default.
+template <class F>
+bool with_shape_cols(const FftAxis& ax, F&& f) {
+    if (ax.cols == 32 && with_shape32(ax.L, f)) return true;
+    if (ax.cols == 8) return with_shape8(ax.L, f);
+    return with_shape(ax.L, f);
+}
+
 template <class F>
 bool with_shape_of(const FftAxis& ax, F&& f) {
     if (ax.lines == 4) return with_shape4(ax.L, f);
@@ -549,7 +575,7 @@ cudaError_t launch_fft2_strided(const FftAxis& ax, int inverse, const float2* in
                                 int in_centred, int n_out, int out_centred, long long inner, long long outer,
                                 cudaStream_t st) {
     cudaError_t err = cudaErrorNotSupported;
-    with_shape(ax.L, [&](auto sh) {
+    with_shape_cols(ax, [&](auto sh) {
         using S = decltype(sh);
         const long long ncolblk = (inner + S::nl - 1) / S::nl;
         const long long nblk = ncolblk * outer;

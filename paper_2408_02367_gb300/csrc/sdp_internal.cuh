@@ -39,6 +39,7 @@ struct FftAxis {
     const float2* tw;
     int generic;   // 1: always the Stockham kernels (a plan's tuning), 0: two-pass where available
     int lines;     // lines per CTA of the fused axis-3 kernels: 0 = default, 8 or 4
+    int cols;      // columns per CTA of the strided axis-1/axis-2 passes: 0 = default, 32 or 8
 };
 
 // A spread subproblem: one chunk of the incidence list of one output bin.

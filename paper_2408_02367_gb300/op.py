@@ -59,7 +59,8 @@ class Tuning(ctypes.Structure):
         ("spread_chunk", ctypes.c_int32),
         ("fft_engine", ctypes.c_int32),
         ("fft_lines", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("fft_cols", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
     @staticmethod
@@ -70,11 +71,12 @@ class Tuning(ctypes.Structure):
         t.spread_chunk = int(d.get("spread_chunk", 512))
         t.fft_engine = int(d.get("fft_engine", 0))
         t.fft_lines = int(d.get("fft_lines", 0))
+        t.fft_cols = int(d.get("fft_cols", 0))
         return t
 
     def as_dict(self):
         return {"spread_bins": tuple(int(v) for v in self.spread_bins), "spread_chunk": int(self.spread_chunk),
-                "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines)}
+                "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines), "fft_cols": int(self.fft_cols)}
 
 
 class Work(ctypes.Structure):

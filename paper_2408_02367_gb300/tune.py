@@ -9,7 +9,8 @@ the operator computes, only how fast it runs on a given trajectory and volume:
 - spread chunk length: incidences per spread CTA (load balance on the dense
   k-space centre against the cost of summing partial tiles);
 - FFT engine: the two-pass register FFTs or the Stockham kernels;
-- FFT lines per CTA of the fused axis-3 prologue and epilogue (16, 8 or 4).
+- FFT lines per CTA of the fused axis-3 prologue and epilogue (16, 8 or 4);
+- FFT columns per CTA of the strided axis-1/axis-2 passes (16, 32 or 8).
 
 `autotune` builds a plan for every candidate on the caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
@@ -35,7 +36,8 @@ DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_
 
 def candidates(full: bool = False):
     """The tunings tried: both bin depths x three chunk lengths with the two-pass
-    FFTs, both bin depths with 8 and 4 FFT lines per CTA, and the Stockham engine on
+    FFTs, both bin depths with 8 and 4 FFT lines per CTA, 32 and 8 strided FFT
+    columns per CTA, and the Stockham engine on
     the default spread; `full` adds more chunks."""
     chunks = (128, 256, 512, 1024, 2048) if full else (256, 512, 1024)
     out = []
@@ -45,6 +47,8 @@ def candidates(full: bool = False):
     for bins in ((8, 4, 8), (8, 4, 4)):
         for lines in (8, 4):
             out.append({"spread_bins": bins, "spread_chunk": 512, "fft_engine": 0, "fft_lines": lines})
+    for cols in (32, 8):
+        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": cols})
     out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
     return out
 

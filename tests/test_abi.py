@@ -102,8 +102,10 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({"fft_lines": 12})                                       # 0, 8 or 4 only
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"fft_cols": 16})                                        # 0, 32 or 8 only
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})
-    t.reserved[1] = 3
+    t.reserved[0] = 3
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})                                                       # valid tuning, no descriptor
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1

@@ -138,6 +138,8 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (8, 4, 8), "spread_chunk": 32, "fft_engine": 1},
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8},
     {"spread_bins": (8, 4, 8), "spread_chunk": 256, "fft_engine": 0, "fft_lines": 4},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": 32},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 8},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, short spread
