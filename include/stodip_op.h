@@ -64,6 +64,9 @@ typedef struct sdp_plan_s* sdp_plan_t;
  *   n[3]           image matrix N1, N2, N3 (axis 3 contiguous), each >= 2.
  *   oversamp       grid oversampling sigma in [1, 4]; the grid length along axis d
  *                  is the smallest even 2,3,5-smooth M_d >= max(ceil(sigma N_d), 2W).
+ *                  M1 M2 M3 K < 2^31 (the K channel grids of one coil, interleaved
+ *                  per grid point, are indexed with 32-bit offsets), else
+ *                  SDP_ERR_UNSUPPORTED.
  *   width          Kaiser-Bessel kernel width W in taps, 2..8.
  *   K              subspace rank (channels of x), 1..16.
  *   T              frames (rows of V), >= 1.

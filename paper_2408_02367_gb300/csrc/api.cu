@@ -64,6 +64,9 @@ struct sdp_plan_s {
     unsigned int* loss_counter = nullptr;
     double* tv_part = nullptr;
     unsigned int* tv_counter = nullptr;
+    // Grid workspaces, channel-interleaved: a call with nk channels holds
+    // [b][i1][i2][i3][kk] (kk fastest), so the W x nk values one row of a
+    // Kaiser-Bessel window touches along axis 3 are one contiguous run.
     float2* bufA = nullptr;
     float2* bufB = nullptr;
     size_t workspace_bytes = 0;
@@ -176,7 +179,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     }
     const long long G = p->M[0] * p->M[1] * p->M[2];
     const long long nvox = p->n[0] * p->n[1] * p->n[2];
-    if (G >= (1LL << 31) || nvox >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
+    // one coil's channel-interleaved grid [M1][M2][M3][K] is indexed with 32-bit offsets
+    if (G * K >= (1LL << 31) || nvox >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
     p->sigma = d->oversamp;
     const double arg = (W / d->oversamp) * (W / d->oversamp) * (d->oversamp - 0.5) * (d->oversamp - 0.5) - 0.8;
     if (!(arg > 0)) return SDP_ERR_UNSUPPORTED;
@@ -471,17 +475,16 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
     const Geo& g = p->geo;
     const long long N1 = g.N[0], N2 = g.N[1];
     const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
-    const long long BK = (long long)B * nk;
     const float2* xs = static_cast<const float2*>(x);
     SDP_TRY(run(p, ST_FWD_FFT3, st, [&] {
         return launch_fwd_prologue_fft3(g, p->ax[2], xs, p->S, coil_idx, B, k0, nk, dinv_axis(p, 0),
                                         dinv_axis(p, 1), dinv_axis(p, 2), p->bufA, p->status, st);
     }));
     SDP_TRY(run(p, ST_FWD_FFT2, st, [&] {
-        return launch_fft_strided(p->ax[1], 0, p->bufA, p->bufB, (int)N2, 1, (int)M2, 0, M3, BK * N1, st);
+        return launch_fft_strided(p->ax[1], 0, p->bufA, p->bufB, (int)N2, 1, (int)M2, 0, M3 * nk, B * N1, st);
     }));
     SDP_TRY(run(p, ST_FWD_FFT1, st, [&] {
-        return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3, BK, st);
+        return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3 * nk, B, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
         return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y),
@@ -496,17 +499,16 @@ int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, i
     const Geo& g = p->geo;
     const long long N1 = g.N[0], N2 = g.N[1];
     const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
-    const long long BK = (long long)B * nk;
     SDP_TRY(run(p, ST_SPREAD, st, [&] {
         return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->wts, p->V,
                              static_cast<const float2*>(y), scale, B, k0, nk, p->bufA, p->partials, p->slots_per_b,
                              p->counters, p->nbins, st);
     }));
     SDP_TRY(run(p, ST_ADJ_FFT1, st, [&] {
-        return launch_fft_strided(p->ax[0], 1, p->bufA, p->bufB, (int)M1, 0, (int)N1, 1, M2 * M3, BK, st);
+        return launch_fft_strided(p->ax[0], 1, p->bufA, p->bufB, (int)M1, 0, (int)N1, 1, M2 * M3 * nk, B, st);
     }));
     SDP_TRY(run(p, ST_ADJ_FFT2, st, [&] {
-        return launch_fft_strided(p->ax[1], 1, p->bufB, p->bufA, (int)M2, 0, (int)N2, 1, M3, BK * N1, st);
+        return launch_fft_strided(p->ax[1], 1, p->bufB, p->bufA, (int)M2, 0, (int)N2, 1, M3 * nk, B * N1, st);
     }));
     SDP_TRY(run(p, ST_ADJ_FFT3, st, [&] {
         return launch_adj_fft3_epilogue(g, p->ax[2], p->bufA, p->S, coil_idx, B, k0, nk, dinv_axis(p, 0),

@@ -198,7 +198,8 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 // Forward A1 fused with the axis-3 FFT.  Lines l = row * nk + kk over
 // row = i1 * N2 + i2; for each coil b of the batch the line is
 // S_c[row][:] x_{k0+kk}[row][:] / psi_hat placed at (i3 - N3/2) mod M3.
-// out[b][kk][row][0..M3).
+// out[b][row][0..M3)[kk] (channel-interleaved; the store has the line index
+// fastest so the channels of one grid point are written together).
 __global__ void __launch_bounds__(kThreads) fwd_prologue_fft3_kernel(
     Geo g, FftAxis ax, const float2* __restrict__ x, const float2* __restrict__ S,
     const int* __restrict__ coil_idx, int B, int k0, int nk, const float* __restrict__ d1,
@@ -240,19 +241,20 @@ __global__ void __launch_bounds__(kThreads) fwd_prologue_fft3_kernel(
         __syncthreads();
         const float2* res = fft_columns<false>(bufa, bufb, tw, ax);
         for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-            const int l = e / L, p = e - (e / L) * L;
+            const int p = e / NL, l = e - (e / NL) * NL;
             const long long gl = l0 + l;
             if (gl < nlines) {
                 const long long row = gl / nk;
                 const int kk = (int)(gl - row * nk);
-                out[(((long long)b * nk + kk) * nrows + row) * L + p] = res[p * NLP + l];
+                out[(((long long)b * nrows + row) * L + p) * nk + kk] = res[p * NLP + l];
             }
         }
         __syncthreads();
     }
 }
 
-// Adjoint axis-3 inverse FFT fused with A7: for each coil b, invert the line,
+// Adjoint axis-3 inverse FFT fused with A7: for each coil b, invert the line
+// (in[b][row][0..M3)[kk], channel-interleaved),
 // keep the N3 centred outputs, multiply by conj(S_c), sum over b, divide by
 // psi_hat and write (or add into) out[k0+kk][row][:].
 __global__ void __launch_bounds__(kThreads) adj_fft3_epilogue_kernel(
@@ -279,13 +281,13 @@ __global__ void __launch_bounds__(kThreads) adj_fft3_epilogue_kernel(
         const bool cok = (c >= 0 && c < g.C);
         if (!cok && threadIdx.x == 0) set_status(status, SDP_ERR_BOUNDS);
         for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-            const int l = e / L, p = e - (e / L) * L;
+            const int p = e / NL, l = e - (e / NL) * NL;
             const long long gl = l0 + l;
             float2 v = make_float2(0.f, 0.f);
             if (gl < nlines) {
                 const long long row = gl / nk;
                 const int kk = (int)(gl - row * nk);
-                v = in[(((long long)b * nk + kk) * nrows + row) * L + p];
+                v = in[(((long long)b * nrows + row) * L + p) * nk + kk];
             }
             bufa[p * NLP + l] = v;
         }

@@ -291,7 +291,9 @@ __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_strided_kernel(const
 // Lines l = row * nk + kk; block (line block, coil b) with the coil index the
 // fastest, so the blocks of all coils of a line block run together and share
 // the x lines in L2.  The line is S_c[row][:] x_{k0+kk}[row][:] / psi_hat
-// placed at (i3 - N3/2) mod M3; out[b][kk][row][0..M3).
+// placed at (i3 - N3/2) mod M3; it is written channel-interleaved,
+// out[b][row][0..M3)[kk], with the lines the fastest thread index of pass 2
+// so that a warp's stores of one grid point's channels are adjacent.
 template <int A, int B, int NLT>
 __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_fwd_prologue_kernel(
     Geo g, const float2* __restrict__ twg, const float2* __restrict__ x, const float2* __restrict__ S,
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_fwd_prologue_kernel(
     }
     __syncthreads();
     if (tid < NLT * A) {
-        const int q1 = tid % A, l2 = tid / A;
+        const int l2 = tid % NLT, q1 = tid / NLT;
         const long long gl = l0 + l2;
         if (gl < nlines) {
             const long long row = gl / nk;
@@ -354,17 +356,20 @@ __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_fwd_prologue_kernel(
                 z[b] = Y[l2 * LP + q1 * B + b];
             });
             RegDft<B, false>::run(z);
-            float2* dst = out + (((long long)bb * nk + kk) * nrows + row) * L;
+            float2* dst = out + (((long long)bb * nrows + row) * L + q1) * nk + kk;
+            const int sq = A * nk;   // outputs q1 + A q2 are A grid points apart
             StaticFor<0, B>::run([&](auto qc) {
                 constexpr int q2 = decltype(qc)::value;
-                dst[q1 + A * q2] = z[q2];
+                dst[q2 * sq] = z[q2];
             });
         }
     }
 }
 
 // ---------------- adjoint axis 3 + epilogue ----------------
-// For each coil of the batch: inverse DFT of the grid line, keep the N3 centred
+// For each coil of the batch: inverse DFT of the grid line (channel-interleaved,
+// in[b][row][0..M3)[kk]; pass 1 has the lines as its fastest thread index so a
+// warp's loads of one grid point's channels are adjacent), keep the N3 centred
 // outputs, multiply by conj(S_c); sum over the batch in registers; divide by
 // psi_hat and write (or add into) out[k0+kk][row][:].
 template <int A, int B, int NLT>
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_adj_epilogue_kernel(
     const long long nvox = nrows * N3;
     const long long l0 = (long long)blockIdx.x * NLT;
     const int h = N3 / 2;
-    const int b1 = tid % B, l1 = tid / B;
+    const int l1 = tid % NLT, b1 = tid / NLT;
     const bool p1 = tid < NLT * B;
     const long long gl1 = l0 + l1;
     const bool line1 = p1 && gl1 < nlines;
@@ -419,10 +424,12 @@ __global__ void __launch_bounds__(NLT*(A > B ? A : B)) fft2_adj_epilogue_kernel(
         if (!cok && tid == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
         if (p1) {
             float2 u[A];
-            const float2* src = in + (((long long)bb * nk + kk1) * nrows + row1) * L;
+            const float2* src = in + (((long long)bb * nrows + row1) * L + b1) * nk + kk1;
+            const int sa = B * nk;   // FFT positions B a + b1 are B grid points apart
             StaticFor<0, A>::run([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                u[a] = line1 ? __ldg(src + B * a + b1) : make_float2(0.f, 0.f);
+                u[a] = line1 ? __ldg(src) : make_float2(0.f, 0.f);
+                src += sa;
             });
             RegDft<A, true>::run(u);
             StaticFor<0, A>::run([&](auto qc) {

@@ -12,12 +12,25 @@
 // trajectory; the plan evaluates them once (kb_weights_kernel) and both this
 // kernel and the spread read them.
 //
-// One warp per sample (samples in bin-sorted order for locality): lanes
-// 0..3W-1 load the 3W one-dimensional weights, every lane then owns
-// ceil(W^3 / 32) taps whose weight and grid offset stay in registers across the
-// B coils and K channels; the W taps along axis 3 are adjacent lanes reading
-// adjacent addresses.  Each lane folds V[t, k] into its partial sum and a
-// butterfly reduction leaves the sample value in lane 0.
+// One warp per sample (samples in bin-sorted order for locality).  The grids
+// are channel-interleaved, [b][i1][i2][i3][kk], so the W taps along axis 3 of
+// one (i1, i2) row of the window, for all nk channels, are one contiguous run
+// of W nk values.
+//
+// Row kernel (nk >= 2): lane l owns the axis-3 tap a3 = l / cg and the channel
+// kk = c0 + l % cg of a group of cg <= 32 / W channels (lanes beyond W cg
+// idle).  Its coefficient phi3(a3) V[t, kk] and its offset within a row are
+// fixed for the sample; for each coil the warp then walks the W^2 rows of the
+// window, one load per lane and row (the warp reads one contiguous run per
+// row), weights them by phi1 phi2 (the same in every lane), multiplies by the
+// lane's coefficient and reduces over the warp.  More than 32 / W channels run
+// as several launches, each adding its groups' sum into y.
+//
+// Tap kernel (nk == 1): lanes own ceil(W^3 / 32) taps each, whose weights and
+// offsets stay in registers across the coils; the W taps of a row are adjacent
+// lanes reading adjacent addresses.
+#include <atomic>
+
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -46,13 +59,152 @@ __global__ void kb_weights_kernel(Geo g, const float4* __restrict__ pts, float* 
     }
 }
 
-template <int W, int CK>
-__global__ void __launch_bounds__(kThreads) interp_kernel(Geo g, const float4* __restrict__ pts,
-                                                         const int* __restrict__ tframe,
-                                                         const float* __restrict__ wts,
-                                                         const float2* __restrict__ V,
-                                                         const float2* __restrict__ grids, int B, int k0, int nk,
-                                                         float2* __restrict__ y, int accumulate) {
+// Sum of W^2 rows of one coil's window for this lane: sum_{a1,a2} phi1 phi2 grid[row(a1, a2) + lane offset].
+template <int W>
+__device__ __forceinline__ void row_loads(const float2* __restrict__ gb, const int (&o1)[W], const int (&o2)[W],
+                                          bool act, float2 (&u)[W][W]) {
+#pragma unroll
+    for (int a1 = 0; a1 < W; ++a1)
+#pragma unroll
+        for (int a2 = 0; a2 < W; ++a2)
+            u[a1][a2] = act ? __ldg(gb + (unsigned)(o1[a1] + o2[a2])) : make_float2(0.f, 0.f);
+}
+
+template <int W>
+__device__ __forceinline__ float2 row_sum(const float (&w1)[W], const float (&w2)[W], const float2 (&u)[W][W]) {
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int a1 = 0; a1 < W; ++a1) {
+        float tx = 0.f, ty = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < W; ++a2) {
+            tx = fmaf(w2[a2], u[a1][a2].x, tx);
+            ty = fmaf(w2[a2], u[a1][a2].y, ty);
+        }
+        sx = fmaf(w1[a1], tx, sx);
+        sy = fmaf(w1[a1], ty, sy);
+    }
+    return make_float2(sx, sy);
+}
+
+__device__ __forceinline__ void put(float2* __restrict__ dst, float ax, float ay, int accumulate) {
+    if (accumulate) {
+        const float2 old = *dst;
+        ax += old.x;
+        ay += old.y;
+    }
+    *dst = make_float2(ax, ay);
+}
+
+// Persistent warps: warp w takes samples w, w + nwarps, ...; the next sample's
+// coordinates, frame and weights are loaded while the current one is
+// interpolated.  For W <= 4 the gathers of two coils are issued together and
+// the two sums share one warp reduction (lanes 0-15 finish coil b, lanes
+// 16-31 coil b + 1).
+template <int W>
+__global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const float4* __restrict__ pts,
+                                                              const int* __restrict__ tframe,
+                                                              const float* __restrict__ wts,
+                                                              const float2* __restrict__ V,
+                                                              const float2* __restrict__ grids, int B, int k0,
+                                                              int nk, int c0, int cg, float2* __restrict__ y,
+                                                              int accumulate) {
+    constexpr bool kPair = W <= 4;
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+    const long long J = g.J;
+    const long long Gk = (long long)M1 * M2 * M3 * nk;   // one coil, all channels of the call
+    const int a3 = lane / cg, kg = lane - a3 * cg;
+    const bool act = a3 < W;
+    const int a3c = act ? a3 : 0;
+    const int kk = c0 + (act ? kg : 0);
+    const int rstride = M3 * nk;                        // one (i1, i2) row
+    float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+    int tn = 0;
+    float wn = 0.f;
+    if (warp0 < J) {
+        pn = __ldg(pts + warp0);
+        tn = __ldg(tframe + warp0);
+        wn = lane < 3 * W ? __ldg(wts + warp0 * (3 * W) + lane) : 0.f;
+    }
+    for (long long s = warp0; s < J; s += nwarps) {
+        const float4 p = pn;
+        const int t = tn;
+        const float wv = wn;
+        const long long sn = s + nwarps;
+        if (sn < J) {
+            pn = __ldg(pts + sn);
+            tn = __ldg(tframe + sn);
+            wn = lane < 3 * W ? __ldg(wts + sn * (3 * W) + lane) : 0.f;
+        }
+        const int orig = __float_as_int(p.w);
+        const int m01 = (int)ceilf(p.x - g.halfW);
+        const int m02 = (int)ceilf(p.y - g.halfW);
+        const int m03 = (int)ceilf(p.z - g.halfW);
+        // this lane's coefficient phi3(a3) V[t, kk] (0 on idle lanes) and offset within a row
+        const float w3 = __shfl_sync(kFull, wv, 2 * W + a3c);
+        const float2 v = act ? __ldg(V + (long long)t * g.K + k0 + kk) : make_float2(0.f, 0.f);
+        const int lofs = wrap1(m03 + a3c, M3) * nk + kk;
+        // row offsets (i1 M2 M3 + i2 M3) nk and the axis-1 / axis-2 weights, the same in every lane
+        float w1[W], w2[W];
+        int o1[W], o2[W];
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            w1[a] = __shfl_sync(kFull, wv, a);
+            w2[a] = __shfl_sync(kFull, wv, W + a);
+            o1[a] = wrap1(m01 + a, M1) * M2 * rstride + lofs;
+            o2[a] = wrap1(m02 + a, M2) * rstride;
+        }
+        const float cx = w3 * v.x, cy = w3 * v.y;
+        int b = 0;
+        if (kPair) {
+            for (; b + 1 < B; b += 2) {
+                const float2* g0 = grids + (long long)b * Gk;
+                float2 u0[W][W], u1[W][W];
+                row_loads<W>(g0, o1, o2, act, u0);
+                row_loads<W>(g0 + Gk, o1, o2, act, u1);
+                const float2 s0 = row_sum<W>(w1, w2, u0);
+                const float2 s1 = row_sum<W>(w1, w2, u1);
+                const float ax0 = cx * s0.x - cy * s0.y, ay0 = cx * s0.y + cy * s0.x;
+                const float ax1 = cx * s1.x - cy * s1.y, ay1 = cx * s1.y + cy * s1.x;
+                // lanes 0-15 keep coil b and send coil b + 1 to lanes 16-31, and back
+                const bool hi = (lane & 16) != 0;
+                float ax = hi ? ax1 : ax0, ay = hi ? ay1 : ay0;
+                ax += __shfl_xor_sync(kFull, hi ? ax0 : ax1, 16);
+                ay += __shfl_xor_sync(kFull, hi ? ay0 : ay1, 16);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    ax += __shfl_xor_sync(kFull, ax, o);
+                    ay += __shfl_xor_sync(kFull, ay, o);
+                }
+                if ((lane & 15) == 0) put(y + (long long)(b + (hi ? 1 : 0)) * J + orig, ax, ay, accumulate);
+            }
+        }
+        for (; b < B; ++b) {
+            float2 u[W][W];
+            row_loads<W>(grids + (long long)b * Gk, o1, o2, act, u);
+            const float2 s0 = row_sum<W>(w1, w2, u);
+            float ax = cx * s0.x - cy * s0.y;
+            float ay = cx * s0.y + cy * s0.x;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(kFull, ax, o);
+                ay += __shfl_xor_sync(kFull, ay, o);
+            }
+            if (lane == 0) put(y + (long long)b * J + orig, ax, ay, accumulate);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) interp_taps_kernel(Geo g, const float4* __restrict__ pts,
+                                                              const int* __restrict__ tframe,
+                                                              const float* __restrict__ wts,
+                                                              const float2* __restrict__ V,
+                                                              const float2* __restrict__ grids, int B, int k0,
+                                                              float2* __restrict__ y, int accumulate) {
     constexpr int W3 = W * W * W;
     constexpr int NIT = (W3 + 31) / 32;
     const int lane = threadIdx.x & 31;
@@ -83,35 +235,20 @@ __global__ void __launch_bounds__(kThreads) interp_kernel(Geo g, const float4* _
             const int i1 = wrap1(m01 + a1, M1), i2 = wrap1(m02 + a2, M2), i3 = wrap1(m03 + a3, M3);
             off[it] = (i1 * M2 + i2) * M3 + i3;
         }
-        const float2* Vt = V + (long long)t * g.K + k0;
+        const float2 v = __ldg(V + (long long)t * g.K + k0);
         for (int b = 0; b < B; ++b) {
-            float ax = 0.f, ay = 0.f;
-            for (int c0 = 0; c0 < nk; c0 += CK) {
-                // all CK x NIT gathers of this channel group are issued before any is used
-                float2 gv[CK][NIT];
+            const float2* gr = grids + (long long)b * G;
+            float2 gv[NIT];
 #pragma unroll
-                for (int q = 0; q < CK; ++q) {
-                    if (CK == 1 || c0 + q < nk) {
-                        const float2* gr = grids + ((long long)b * nk + c0 + q) * G;
+            for (int it = 0; it < NIT; ++it) gv[it] = __ldg(gr + off[it]);
+            float sx = 0.f, sy = 0.f;
 #pragma unroll
-                        for (int it = 0; it < NIT; ++it) gv[q][it] = __ldg(gr + off[it]);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < CK; ++q) {
-                    if (CK == 1 || c0 + q < nk) {
-                        float sx = 0.f, sy = 0.f;
-#pragma unroll
-                        for (int it = 0; it < NIT; ++it) {
-                            sx = fmaf(wt[it], gv[q][it].x, sx);
-                            sy = fmaf(wt[it], gv[q][it].y, sy);
-                        }
-                        const float2 v = __ldg(Vt + c0 + q);
-                        ax += v.x * sx - v.y * sy;
-                        ay += v.x * sy + v.y * sx;
-                    }
-                }
+            for (int it = 0; it < NIT; ++it) {
+                sx = fmaf(wt[it], gv[it].x, sx);
+                sy = fmaf(wt[it], gv[it].y, sy);
             }
+            float ax = v.x * sx - v.y * sy;
+            float ay = v.x * sy + v.y * sx;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 ax += __shfl_xor_sync(kFull, ax, o);
@@ -130,28 +267,42 @@ __global__ void __launch_bounds__(kThreads) interp_kernel(Geo g, const float4* _
     }
 }
 
-template <int W, int CK>
-cudaError_t launch_wk(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
-                      const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
-    const long long warps_per_block = kThreads / 32;
-    long long nblk = ((long long)g.J + warps_per_block - 1) / warps_per_block;
-    if (nblk > 0x7fffffffLL) nblk = 0x7fffffffLL;
-    interp_kernel<W, CK><<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, y,
-                                                              accumulate);
-    return cudaGetLastError();
-}
-
 template <int W>
 cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
                      const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
-    switch (channel_group(nk)) {
-        case 1: return launch_wk<W, 1>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 2: return launch_wk<W, 2>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 3: return launch_wk<W, 3>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 4: return launch_wk<W, 4>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 5: return launch_wk<W, 5>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        default: return launch_wk<W, 8>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+    const long long warps_per_block = kThreads / 32;
+    long long nblk = ((long long)g.J + warps_per_block - 1) / warps_per_block;
+    if (nblk > 0x7fffffffLL) nblk = 0x7fffffffLL;
+    if (nk == 1) {
+        interp_taps_kernel<W><<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, y,
+                                                                  accumulate);
+        return cudaGetLastError();
     }
+    // persistent grid: the CTAs that are resident at once (or fewer for a short trajectory)
+    static std::atomic<int> resident{0};
+    int per_sm = resident.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_rows_kernel<W>, kThreads, 0) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        resident.store(per_sm, std::memory_order_relaxed);
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm < 1)
+        return cudaErrorInvalidDevice;
+    const long long nres = (long long)nsm * per_sm;
+    const unsigned nrow = (unsigned)(nblk < nres ? nblk : nres);
+    constexpr int kGroup = 32 / W;   // channels per launch
+    for (int c0 = 0; c0 < nk; c0 += kGroup) {
+        const int cg = nk - c0 < kGroup ? nk - c0 : kGroup;
+        interp_rows_kernel<W><<<nrow, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
+                                                        accumulate || c0 > 0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (c0 > 0) note_launches(1);   // the stage counts its first launch
+    }
+    return cudaSuccess;
 }
 
 }  // namespace

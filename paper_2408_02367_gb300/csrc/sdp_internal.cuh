@@ -66,10 +66,6 @@ struct Geo {
     float halfW;
 };
 
-// Compile-time channel-group size of the interpolation and spread kernels for
-// nk channels: exact for 1..5, groups of 8 above.
-inline int channel_group(int nk) { return nk <= 5 ? nk : 8; }
-
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
 // Spread bin shapes with a kernel: 8 x 4 x 8 and 8 x 4 x 4 grid points.
 bool spread_bins_supported(const int bs[3]);

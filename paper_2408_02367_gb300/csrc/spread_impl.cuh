@@ -20,8 +20,11 @@
 //     multi-chunk bin (the dense k-space centre): each chunk stores a partial
 //     tile and the last chunk to finish (device-scope counter, no waiting)
 //     sums the partials in chunk order and stores the bin.
-// Every grid point is written exactly once by plain 16-byte stores: no zero
-// fill of the grid, no atomics on it and no shared-memory accumulation.
+// Every grid point is written exactly once by plain stores: no zero fill of
+// the grid, no atomics on it and no shared-memory accumulation.  The grid is
+// channel-interleaved ([b][i1][i2][i3][kk]), so a lane's column of B3 points x
+// nk channels is one contiguous run, stored 16 bytes at a time when the call's
+// channels form one group.
 #pragma once
 
 #include "sdp_internal.cuh"
@@ -69,6 +72,34 @@ __device__ __forceinline__ float4 pair4(unsigned long long a, unsigned long long
     asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
     asm("mov.b64 {%0, %1}, %2;" : "=f"(r.z), "=f"(r.w) : "l"(b));
     return r;
+}
+
+__device__ __forceinline__ unsigned long long pack2(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+
+// Store a lane's column: v[x3][q] goes to gcol[x3 * nk + q] for x3 < x3end.
+// With all nk channels in this group the B3 * NK values are contiguous and
+// go out as 16-byte pairs (gcol is 16-byte aligned: M3 and lo3 are even, so
+// is x3end, and a pair never straddles x3end); otherwise 8-byte stores.
+template <int B3, int NK>
+__device__ __forceinline__ void store_column(float2* gcol, int nk, int x3end,
+                                             const unsigned long long (&v)[B3][NK]) {
+    if (NK == nk) {
+#pragma unroll
+        for (int e = 0; e < B3 * NK; e += 2)
+            if (e < x3end * NK)
+                *reinterpret_cast<float4*>(gcol + e) = pair4(v[e / NK][e % NK], v[(e + 1) / NK][(e + 1) % NK]);
+    } else {
+#pragma unroll
+        for (int x3 = 0; x3 < B3; ++x3)
+            if (x3 < x3end)
+#pragma unroll
+                for (int q = 0; q < NK; ++q)
+                    *reinterpret_cast<unsigned long long*>(gcol + (long long)x3 * nk + q) = v[x3][q];
+    }
 }
 
 template <int B3, int W, int NK>
@@ -189,32 +220,23 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
         __syncwarp();
     }
 
-    // store: this lane's column, two points per 16-byte store (M3, lo3 even)
+    // store: this lane's column, element (x3, q) at gcol[x3 * nk + q]
     const int j1 = lo1 + x1, j2 = lo2 + x2;
-    float2* gcol = a.grids + ((long long)b * a.nk + kofs) * G + ((long long)j1 * M2 + j2) * M3 + lo3;
+    const int nk = a.nk;
+    float2* gcol = a.grids + (long long)b * G * nk + (((long long)j1 * M2 + j2) * M3 + lo3) * nk + kofs;
     const bool colok = j1 < M1 && j2 < M2;
+    const int x3end = min(B3, M3 - lo3);
     if (sp.nchunks == 1) {
-        if (colok) {
-#pragma unroll
-            for (int q = 0; q < NK; ++q)
-#pragma unroll
-                for (int x3 = 0; x3 < B3; x3 += 2)
-                    if (lo3 + x3 < M3)
-                        *reinterpret_cast<float4*>(gcol + q * G + x3) =
-                            pair4(acc[x3][q], acc[x3 + 1][q]);
-        }
+        if (colok) store_column<B3, NK>(gcol, nk, x3end, acc);
         return;
     }
-    // multi-chunk bin: partial columns [q][lane][x3] in the chunk's slot; the last chunk sums them
+    // multi-chunk bin: partial columns [lane][x3][q] in the chunk's slot; the last chunk sums them
+    constexpr int CE = B3 * NK;   // values of a lane's column (even)
     float4* part = reinterpret_cast<float4*>(a.partials +
                                              ((long long)b * a.slots_per_b + sp.slot + sp.chunk) * a.slot_elems +
-                                             (long long)kofs * BP);
+                                             (long long)kofs * BP + lane * CE);
 #pragma unroll
-    for (int q = 0; q < NK; ++q)
-#pragma unroll
-        for (int x3 = 0; x3 < B3; x3 += 2)
-            part[(q * BP + lane * B3 + x3) / 2] =
-                pair4(acc[x3][q], acc[x3 + 1][q]);
+    for (int e = 0; e < CE; e += 2) part[e / 2] = pair4(acc[e / NK][e % NK], acc[(e + 1) / NK][(e + 1) % NK]);
     __threadfence();
     __syncwarp();
     int last = 0;
@@ -225,23 +247,21 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     if (!last) return;
     __threadfence();
     const float2* part0 =
-        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP;
+        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP + lane * CE;
 #pragma unroll
-    for (int q = 0; q < NK; ++q) {
-#pragma unroll
-        for (int x3 = 0; x3 < B3; x3 += 2) {
-            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int ch = 0; ch < sp.nchunks; ++ch) {
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(part0 + ch * a.slot_elems) +
-                                        (q * BP + lane * B3 + x3) / 2);
-                sum.x += v.x;
-                sum.y += v.y;
-                sum.z += v.z;
-                sum.w += v.w;
-            }
-            if (colok && lo3 + x3 < M3) *reinterpret_cast<float4*>(gcol + q * G + x3) = sum;
+    for (int e = 0; e < CE; e += 2) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ch = 0; ch < sp.nchunks; ++ch) {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(part0 + ch * a.slot_elems) + e / 2);
+            sum.x += v.x;
+            sum.y += v.y;
+            sum.z += v.z;
+            sum.w += v.w;
         }
+        acc[e / NK][e % NK] = pack2(sum.x, sum.y);
+        acc[(e + 1) / NK][(e + 1) % NK] = pack2(sum.z, sum.w);
     }
+    if (colok) store_column<B3, NK>(gcol, nk, x3end, acc);
     if (lane == 0) a.counters[((long long)b * a.ngroups + a.group) * a.nbins + sp.bin] = 0;
 }
 
@@ -273,6 +293,7 @@ cudaError_t launch_w(SpreadArgs a, int nsub, int B, cudaStream_t st) {
             default: e = launch_wk<B3, W, 8>(a, kofs, nsub, B, st); break;
         }
         if (e != cudaSuccess) return e;
+        if (gi > 0) note_launches(1);   // the stage counts its first launch
     }
     return cudaSuccess;
 }

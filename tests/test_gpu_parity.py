@@ -79,6 +79,10 @@ CASES = {
     "fft2_250_axis1": ((200, 8, 10), 4, 1.25, 3, 2, 5, 1, 300, [1]),
     "fft2_200_250": ((8, 160, 200), 4, 1.25, 2, 2, 4, 1, 300, [0, 1]),
     "fft2_240_256": ((120, 8, 128), 4, 2.0, 1, 1, 3, 1, 200, [0]),
+    # channel groups: interpolation runs 32 // W channels per launch (W=6: 5 + 2),
+    # the spread 8 per launch (K=10: 8 + 2, 8-byte column stores)
+    "w6_k7_groups": ((18, 20, 16), 6, 2.0, 7, 2, 9, 1, 300, [1, 0]),
+    "w4_k10_groups": ((16, 16, 16), 4, 1.25, 10, 2, 12, 1, 400, [0, 1]),
 }
 
 
@@ -225,6 +229,27 @@ def test_channel_split_and_plain_form_equal_batched():
     # accumulate flag of the full adjoint
     a2 = A.adjoint(r, ci, out=a.clone(), accumulate=True)
     assert (torch.linalg.norm(a2 - 2 * a) / torch.linalg.norm(2 * a)).item() < 1e-6
+
+
+def test_channel_subsets_sum_to_the_full_call():
+    """Calls on channel ranges [k0, k0 + nk) with nk > 1 (grids interleaved over nk
+    channels, not K) add up to the call on all K channels."""
+    c = make_case((18, 16, 20), 4, 1.25, 7, 3, 12, 1, 256, [2, 0])
+    A = gpu_op(c)
+    x = t(c["x"])
+    ci = t(c["coils"])
+    y = A.forward(x, ci)
+    r = t(synth.random_complex((2, A.J), 4))
+    a = A.adjoint(r, ci)
+    for split in ((0, 3, 7), (0, 2, 5, 7), (0, 6, 7)):
+        ys = torch.zeros_like(y)
+        as_ = torch.zeros_like(a)
+        for k0, k1 in zip(split[:-1], split[1:]):
+            A.forward(x, ci, out=ys, k0=k0, nk=k1 - k0, accumulate=True)
+            A.adjoint(r, ci, out=as_, k0=k0, nk=k1 - k0, accumulate=True)
+        assert (torch.linalg.norm(ys - y) / torch.linalg.norm(y)).item() < 1e-5, split
+        assert (torch.linalg.norm(as_ - a) / torch.linalg.norm(a)).item() < 1e-5, split
+    assert A.status() == 0
 
 
 def test_bad_coil_index_sets_status_without_fault():
