@@ -59,32 +59,51 @@ __global__ void kb_weights_kernel(Geo g, const float4* __restrict__ pts, float* 
     }
 }
 
-// Sum of W^2 rows of one coil's window for this lane: sum_{a1,a2} phi1 phi2 grid[row(a1, a2) + lane offset].
-template <int W>
-__device__ __forceinline__ void row_loads(const float2* __restrict__ gb, const int (&o1)[W], const int (&o2)[W],
-                                          bool act, float2 (&u)[W][W]) {
-#pragma unroll
-    for (int a1 = 0; a1 < W; ++a1)
-#pragma unroll
-        for (int a2 = 0; a2 < W; ++a2)
-            u[a1][a2] = act ? __ldg(gb + (unsigned)(o1[a1] + o2[a2])) : make_float2(0.f, 0.f);
+// Packed (Re, Im) pairs for fma.rn.f32x2: both components with one instruction,
+// each rounded as a scalar fmaf would be.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
+// The W^2 row values of one coil's window at this lane's offset (every lane
+// loads: idle lanes repeat the last active lane's address and carry a zero
+// coefficient).
 template <int W>
-__device__ __forceinline__ float2 row_sum(const float (&w1)[W], const float (&w2)[W], const float2 (&u)[W][W]) {
-    float sx = 0.f, sy = 0.f;
+__device__ __forceinline__ void row_loads(const float2* __restrict__ gb, const int (&o1)[W], const int (&o2)[W],
+                                          unsigned long long (&u)[W][W]) {
 #pragma unroll
     for (int a1 = 0; a1 < W; ++a1) {
-        float tx = 0.f, ty = 0.f;
+        const unsigned long long* r = reinterpret_cast<const unsigned long long*>(gb + (unsigned)o1[a1]);
 #pragma unroll
-        for (int a2 = 0; a2 < W; ++a2) {
-            tx = fmaf(w2[a2], u[a1][a2].x, tx);
-            ty = fmaf(w2[a2], u[a1][a2].y, ty);
-        }
-        sx = fmaf(w1[a1], tx, sx);
-        sy = fmaf(w1[a1], ty, sy);
+        for (int a2 = 0; a2 < W; ++a2) u[a1][a2] = __ldg(r + (unsigned)o2[a2]);
     }
-    return make_float2(sx, sy);
+}
+
+// sum_{a1} phi1(a1) sum_{a2} phi2(a2) u[a1][a2], as a (Re, Im) pair.
+template <int W>
+__device__ __forceinline__ float2 row_sum(const unsigned long long (&w1)[W], const unsigned long long (&w2)[W],
+                                          const unsigned long long (&u)[W][W]) {
+    unsigned long long acc = 0ull;
+#pragma unroll
+    for (int a1 = 0; a1 < W; ++a1) {
+        unsigned long long t = 0ull;
+#pragma unroll
+        for (int a2 = 0; a2 < W; ++a2) t = fma2(w2[a2], u[a1][a2], t);
+        acc = fma2(w1[a1], t, acc);
+    }
+    return upk2(acc);
 }
 
 __device__ __forceinline__ void put(float2* __restrict__ dst, float ax, float ay, int accumulate) {
@@ -96,13 +115,20 @@ __device__ __forceinline__ void put(float2* __restrict__ dst, float ax, float ay
     *dst = make_float2(ax, ay);
 }
 
-// Persistent warps: warp w takes samples w, w + nwarps, ...; the next sample's
-// coordinates, frame and weights are loaded while the current one is
-// interpolated.  For W <= 4 the gathers of two coils are issued together and
+// Persistent CTAs of NT threads: warp w of CTA c takes the bin-sorted samples
+// c (NT/32) + w + k gridDim.x (NT/32), k = 0, 1, ...: the whole grid of warps
+// moves through one window of consecutive samples (their windows overlap, so
+// most gathers hit L2), and the warps of a CTA, resident on one SM, take
+// neighbouring samples (their gathers share the SM's L1).  For W <= 4 one
+// 1024-thread CTA fills an SM.  The next sample's coordinates, frame and
+// weights are loaded while the current one is interpolated.  For W <= 4 the gathers of two coils are issued together and
 // the two sums share one warp reduction (lanes 0-15 finish coil b, lanes
 // 16-31 coil b + 1).
 template <int W>
-__global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const float4* __restrict__ pts,
+constexpr int rows_threads() { return W <= 4 ? 1024 : 256; }
+
+template <int W, int NT = rows_threads<W>()>
+__global__ void __launch_bounds__(NT) interp_rows_kernel(Geo g, const float4* __restrict__ pts,
                                                               const int* __restrict__ tframe,
                                                               const float* __restrict__ wts,
                                                               const float2* __restrict__ V,
@@ -111,29 +137,31 @@ __global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const floa
                                                               int accumulate) {
     constexpr bool kPair = W <= 4;
     const int lane = threadIdx.x & 31;
-    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
     const long long J = g.J;
+    const long long first = ((long long)blockIdx.x * NT + threadIdx.x) >> 5;
+    const long long step = ((long long)gridDim.x * NT) >> 5;
+    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
     const long long Gk = (long long)M1 * M2 * M3 * nk;   // one coil, all channels of the call
     const int a3 = lane / cg, kg = lane - a3 * cg;
     const bool act = a3 < W;
-    const int a3c = act ? a3 : 0;
-    const int kk = c0 + (act ? kg : 0);
+    // idle lanes repeat the last active lane's tap and channel (an address the warp
+    // reads anyway); their coefficient is zero
+    const int a3c = act ? a3 : W - 1;
+    const int kk = c0 + (act ? kg : cg - 1);
     const int rstride = M3 * nk;                        // one (i1, i2) row
     float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
     int tn = 0;
     float wn = 0.f;
-    if (warp0 < J) {
-        pn = __ldg(pts + warp0);
-        tn = __ldg(tframe + warp0);
-        wn = lane < 3 * W ? __ldg(wts + warp0 * (3 * W) + lane) : 0.f;
+    if (first < J) {
+        pn = __ldg(pts + first);
+        tn = __ldg(tframe + first);
+        wn = lane < 3 * W ? __ldg(wts + first * (3 * W) + lane) : 0.f;
     }
-    for (long long s = warp0; s < J; s += nwarps) {
+    for (long long s = first; s < J; s += step) {
         const float4 p = pn;
         const int t = tn;
         const float wv = wn;
-        const long long sn = s + nwarps;
+        const long long sn = s + step;
         if (sn < J) {
             pn = __ldg(pts + sn);
             tn = __ldg(tframe + sn);
@@ -147,13 +175,16 @@ __global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const floa
         const float w3 = __shfl_sync(kFull, wv, 2 * W + a3c);
         const float2 v = act ? __ldg(V + (long long)t * g.K + k0 + kk) : make_float2(0.f, 0.f);
         const int lofs = wrap1(m03 + a3c, M3) * nk + kk;
-        // row offsets (i1 M2 M3 + i2 M3) nk and the axis-1 / axis-2 weights, the same in every lane
-        float w1[W], w2[W];
+        // row offsets (i1 M2 M3 + i2 M3) nk and the axis-1 / axis-2 weights (as (w, w)
+        // pairs), the same in every lane
+        unsigned long long w1[W], w2[W];
         int o1[W], o2[W];
 #pragma unroll
         for (int a = 0; a < W; ++a) {
-            w1[a] = __shfl_sync(kFull, wv, a);
-            w2[a] = __shfl_sync(kFull, wv, W + a);
+            const float v1 = __shfl_sync(kFull, wv, a);
+            const float v2 = __shfl_sync(kFull, wv, W + a);
+            w1[a] = pk2(v1, v1);
+            w2[a] = pk2(v2, v2);
             o1[a] = wrap1(m01 + a, M1) * M2 * rstride + lofs;
             o2[a] = wrap1(m02 + a, M2) * rstride;
         }
@@ -162,9 +193,9 @@ __global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const floa
         if (kPair) {
             for (; b + 1 < B; b += 2) {
                 const float2* g0 = grids + (long long)b * Gk;
-                float2 u0[W][W], u1[W][W];
-                row_loads<W>(g0, o1, o2, act, u0);
-                row_loads<W>(g0 + Gk, o1, o2, act, u1);
+                unsigned long long u0[W][W], u1[W][W];
+                row_loads<W>(g0, o1, o2, u0);
+                row_loads<W>(g0 + Gk, o1, o2, u1);
                 const float2 s0 = row_sum<W>(w1, w2, u0);
                 const float2 s1 = row_sum<W>(w1, w2, u1);
                 const float ax0 = cx * s0.x - cy * s0.y, ay0 = cx * s0.y + cy * s0.x;
@@ -183,8 +214,8 @@ __global__ void __launch_bounds__(kThreads) interp_rows_kernel(Geo g, const floa
             }
         }
         for (; b < B; ++b) {
-            float2 u[W][W];
-            row_loads<W>(grids + (long long)b * Gk, o1, o2, act, u);
+            unsigned long long u[W][W];
+            row_loads<W>(grids + (long long)b * Gk, o1, o2, u);
             const float2 s0 = row_sum<W>(w1, w2, u);
             float ax = cx * s0.x - cy * s0.y;
             float ay = cx * s0.y + cy * s0.x;
@@ -273,6 +304,7 @@ cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const f
     const long long warps_per_block = kThreads / 32;
     long long nblk = ((long long)g.J + warps_per_block - 1) / warps_per_block;
     if (nblk > 0x7fffffffLL) nblk = 0x7fffffffLL;
+    constexpr int NT = rows_threads<W>();
     if (nk == 1) {
         interp_taps_kernel<W><<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, y,
                                                                   accumulate);
@@ -282,8 +314,8 @@ cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const f
     static std::atomic<int> resident{0};
     int per_sm = resident.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_rows_kernel<W>, kThreads, 0) !=
-                cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_rows_kernel<W>, NT, 0) != cudaSuccess ||
+            per_sm < 1)
             per_sm = 1;
         resident.store(per_sm, std::memory_order_relaxed);
     }
@@ -292,12 +324,13 @@ cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const f
                                                   cudaSuccess || nsm < 1)
         return cudaErrorInvalidDevice;
     const long long nres = (long long)nsm * per_sm;
-    const unsigned nrow = (unsigned)(nblk < nres ? nblk : nres);
+    const long long nneed = ((long long)g.J + NT / 32 - 1) / (NT / 32);
+    const unsigned nrow = (unsigned)(nneed < nres ? nneed : nres);
     constexpr int kGroup = 32 / W;   // channels per launch
     for (int c0 = 0; c0 < nk; c0 += kGroup) {
         const int cg = nk - c0 < kGroup ? nk - c0 : kGroup;
-        interp_rows_kernel<W><<<nrow, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
-                                                        accumulate || c0 > 0);
+        interp_rows_kernel<W><<<nrow, NT, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
+                                                  accumulate || c0 > 0);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (c0 > 0) note_launches(1);   // the stage counts its first launch
