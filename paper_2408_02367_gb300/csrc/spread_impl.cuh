@@ -80,25 +80,47 @@ __device__ __forceinline__ unsigned long long pack2(float x, float y) {
     return r;
 }
 
-// Store a lane's column: v[x3][q] goes to gcol[x3 * nk + q] for x3 < x3end.
-// With all nk channels in this group the B3 * NK values are contiguous and
-// go out as 16-byte pairs (gcol is 16-byte aligned: M3 and lo3 are even, so
-// is x3end, and a pair never straddles x3end); otherwise 8-byte stores.
+// Store the bin: lane l's column (x1, x2) = (l / 4, l % 4) holds v[x3][q], which
+// goes to gbin[x1 cs1 + x2 cs2 + x3 nk + q] for x1 < n1, x2 < n2, x3 < x3end.
+// With all nk channels in this group the column's B3 NK values are contiguous:
+// the lanes first write their columns to shared memory (tr, CQ 16-byte pairs
+// each at an odd stride TS, so a quarter-warp's 16-byte writes hit distinct
+// banks), then the warp stores pair e of column e / CQ for e = lane, lane + 32,
+// ..., so consecutive lanes write consecutive pieces of one column run (a
+// store instruction covers whole runs instead of 32 lines).  All 16-byte
+// aligned: M3, lo3 and x3end are even, so a pair never straddles x3end.
+// Otherwise (channel groups) each lane stores its own column, 8 bytes at a time.
 template <int B3, int NK>
-__device__ __forceinline__ void store_column(float2* gcol, int nk, int x3end,
-                                             const unsigned long long (&v)[B3][NK]) {
+__device__ __forceinline__ void store_bin(float4* tr, const unsigned long long (&v)[B3][NK], float2* gbin,
+                                          long long cs1, long long cs2, int n1, int n2, int x3end, int nk,
+                                          int lane) {
+    constexpr int CQ = B3 * NK / 2;
+    constexpr int TS = CQ | 1;
     if (NK == nk) {
+        __syncwarp();
 #pragma unroll
-        for (int e = 0; e < B3 * NK; e += 2)
-            if (e < x3end * NK)
-                *reinterpret_cast<float4*>(gcol + e) = pair4(v[e / NK][e % NK], v[(e + 1) / NK][(e + 1) % NK]);
+        for (int j = 0; j < CQ; ++j)
+            tr[lane * TS + j] = pair4(v[(2 * j) / NK][(2 * j) % NK], v[(2 * j + 1) / NK][(2 * j + 1) % NK]);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < CQ; ++r) {
+            const int e = r * 32 + lane;
+            const int c = e / CQ, j = e - c * CQ;
+            const int c1 = c >> 2, c2 = c & 3;
+            if (c1 < n1 && c2 < n2 && 2 * j < x3end * NK)
+                *reinterpret_cast<float4*>(gbin + c1 * cs1 + c2 * cs2 + 2 * j) = tr[c * TS + j];
+        }
     } else {
+        const int x1 = lane >> 2, x2 = lane & 3;
+        if (x1 < n1 && x2 < n2) {
+            float2* gcol = gbin + x1 * cs1 + x2 * cs2;
 #pragma unroll
-        for (int x3 = 0; x3 < B3; ++x3)
-            if (x3 < x3end)
+            for (int x3 = 0; x3 < B3; ++x3)
+                if (x3 < x3end)
 #pragma unroll
-                for (int q = 0; q < NK; ++q)
-                    *reinterpret_cast<unsigned long long*>(gcol + (long long)x3 * nk + q) = v[x3][q];
+                    for (int q = 0; q < NK; ++q)
+                        *reinterpret_cast<unsigned long long*>(gcol + (long long)x3 * nk + q) = v[x3][q];
+        }
     }
 }
 
@@ -107,10 +129,15 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     constexpr int BP = B1 * B2 * B3;
     constexpr int NW = 3 * W;
     constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
-    __shared__ float psm[32 * NP];            // [incidence][x1 (8) | x2 (4)], 0 outside the window
-    __shared__ float2 p3sm[32 * B3];          // [incidence][x3]: (w3, w3), 0 outside the window
-    __shared__ unsigned msm[32];              // axis-3 positions the window covers (bit x3)
-    __shared__ float2 csm[32 * NK];
+    // staging of 32 incidences, reused for the bin's store once they are summed
+    constexpr int kStage = 32 * B3 * 8 + 32 * NK * 8 + 32 * NP * 4 + 32 * 4;
+    constexpr int kTr = 32 * ((B3 * NK / 2) | 1) * 16;
+    __shared__ __align__(16) unsigned char sraw[kStage > kTr ? kStage : kTr];
+    float2* p3sm = reinterpret_cast<float2*>(sraw);  // [incidence][x3]: (w3, w3), 0 outside the window
+    float2* csm = p3sm + 32 * B3;                      // [incidence][k]: conj(V[t, k]) r
+    float* psm = reinterpret_cast<float*>(csm + 32 * NK);   // [incidence][x1 (8) | x2 (4)], 0 outside
+    unsigned* msm = reinterpret_cast<unsigned*>(psm + 32 * NP);   // axis-3 positions covered (bit x3)
+    float4* tr = reinterpret_cast<float4*>(sraw);
     const Geo& g = a.g;
     const int lane = threadIdx.x;
     const int x1 = lane >> 2, x2 = lane & 3;
@@ -220,23 +247,25 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
         __syncwarp();
     }
 
-    // store: this lane's column, element (x3, q) at gcol[x3 * nk + q]
-    const int j1 = lo1 + x1, j2 = lo2 + x2;
+    // store: column (x1, x2) of the bin, element (x3, q) at gbin[x1 cs1 + x2 cs2 + x3 nk + q]
     const int nk = a.nk;
-    float2* gcol = a.grids + (long long)b * G * nk + (((long long)j1 * M2 + j2) * M3 + lo3) * nk + kofs;
-    const bool colok = j1 < M1 && j2 < M2;
+    const long long cs2 = (long long)M3 * nk, cs1 = (long long)M2 * cs2;
+    float2* gbin = a.grids + (long long)b * G * nk + (((long long)lo1 * M2 + lo2) * M3 + lo3) * nk + kofs;
+    const int n1 = M1 - lo1, n2 = M2 - lo2;
     const int x3end = min(B3, M3 - lo3);
     if (sp.nchunks == 1) {
-        if (colok) store_column<B3, NK>(gcol, nk, x3end, acc);
+        store_bin<B3, NK>(tr, acc, gbin, cs1, cs2, n1, n2, x3end, nk, lane);
         return;
     }
-    // multi-chunk bin: partial columns [lane][x3][q] in the chunk's slot; the last chunk sums them
-    constexpr int CE = B3 * NK;   // values of a lane's column (even)
+    // multi-chunk bin: the chunk's partial tile in its slot, 16-byte pair j of lane l at
+    // [j][l] (each store instruction writes 512 contiguous bytes); the last chunk sums them
+    constexpr int CQ = B3 * NK / 2;
     float4* part = reinterpret_cast<float4*>(a.partials +
                                              ((long long)b * a.slots_per_b + sp.slot + sp.chunk) * a.slot_elems +
-                                             (long long)kofs * BP + lane * CE);
+                                             (long long)kofs * BP);
 #pragma unroll
-    for (int e = 0; e < CE; e += 2) part[e / 2] = pair4(acc[e / NK][e % NK], acc[(e + 1) / NK][(e + 1) % NK]);
+    for (int j = 0; j < CQ; ++j)
+        part[j * 32 + lane] = pair4(acc[(2 * j) / NK][(2 * j) % NK], acc[(2 * j + 1) / NK][(2 * j + 1) % NK]);
     __threadfence();
     __syncwarp();
     int last = 0;
@@ -246,22 +275,23 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     last = __shfl_sync(kFull, last, 0);
     if (!last) return;
     __threadfence();
-    const float2* part0 =
-        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP + lane * CE;
+    const float4* part0 = reinterpret_cast<const float4*>(
+        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP);
+    const long long slot4 = a.slot_elems / 2;
 #pragma unroll
-    for (int e = 0; e < CE; e += 2) {
+    for (int j = 0; j < CQ; ++j) {
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int ch = 0; ch < sp.nchunks; ++ch) {
-            const float4 v = __ldcg(reinterpret_cast<const float4*>(part0 + ch * a.slot_elems) + e / 2);
+            const float4 v = __ldcg(part0 + ch * slot4 + j * 32 + lane);
             sum.x += v.x;
             sum.y += v.y;
             sum.z += v.z;
             sum.w += v.w;
         }
-        acc[e / NK][e % NK] = pack2(sum.x, sum.y);
-        acc[(e + 1) / NK][(e + 1) % NK] = pack2(sum.z, sum.w);
+        acc[(2 * j) / NK][(2 * j) % NK] = pack2(sum.x, sum.y);
+        acc[(2 * j + 1) / NK][(2 * j + 1) % NK] = pack2(sum.z, sum.w);
     }
-    if (colok) store_column<B3, NK>(gcol, nk, x3end, acc);
+    store_bin<B3, NK>(tr, acc, gbin, cs1, cs2, n1, n2, x3end, nk, lane);
     if (lane == 0) a.counters[((long long)b * a.ngroups + a.group) * a.nbins + sp.bin] = 0;
 }
 
