@@ -129,13 +129,16 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     constexpr int BP = B1 * B2 * B3;
     constexpr int NW = 3 * W;
     constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
-    // staging of 32 incidences, reused for the bin's store once they are summed
-    constexpr int kStage = 32 * B3 * 8 + 32 * NK * 8 + 32 * NP * 4 + 32 * 4;
+    // staging of 32 incidences, reused for the bin's store once they are summed; the
+    // channel coefficients of an incidence sit at an even stride NKP so that they, like
+    // the B3 (w3, w3) pairs, are read 16 bytes at a time
+    constexpr int NKP = (NK + 1) & ~1;
+    constexpr int kStage = 32 * B3 * 8 + 32 * NKP * 8 + 32 * NP * 4 + 32 * 4;
     constexpr int kTr = 32 * ((B3 * NK / 2) | 1) * 16;
     __shared__ __align__(16) unsigned char sraw[kStage > kTr ? kStage : kTr];
     float2* p3sm = reinterpret_cast<float2*>(sraw);  // [incidence][x3]: (w3, w3), 0 outside the window
     float2* csm = p3sm + 32 * B3;                      // [incidence][k]: conj(V[t, k]) r
-    float* psm = reinterpret_cast<float*>(csm + 32 * NK);   // [incidence][x1 (8) | x2 (4)], 0 outside
+    float* psm = reinterpret_cast<float*>(csm + 32 * NKP);  // [incidence][x1 (8) | x2 (4)], 0 outside
     unsigned* msm = reinterpret_cast<unsigned*>(psm + 32 * NP);   // axis-3 positions covered (bit x3)
     float4* tr = reinterpret_cast<float4*>(sraw);
     const Geo& g = a.g;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
 #pragma unroll
             for (int q = 0; q < NK; ++q) {
                 const float2 v = __ldg(Vt + q);
-                csm[lane * NK + q] = make_float2(v.x * r.x + v.y * r.y, v.x * r.y - v.y * r.x);
+                csm[lane * NKP + q] = make_float2(v.x * r.x + v.y * r.y, v.x * r.y - v.y * r.x);
             }
         }
         __syncwarp();
@@ -227,11 +230,21 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
             const float w12 = pw[x1] * pw[B1 + x2];
             unsigned long long w12p;
             asm("mov.b64 %0, {%1, %1};" : "=l"(w12p) : "f"(w12));
-            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(csm + i * NK);
-            const unsigned long long* wp3 = reinterpret_cast<const unsigned long long*>(p3sm + i * B3);
-            unsigned long long c[NK];
+            const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(csm + i * NKP);
+            const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(p3sm + i * B3);
+            unsigned long long c[NK], wp3[B3];
 #pragma unroll
-            for (int q = 0; q < NK; ++q) c[q] = cp[q];
+            for (int q = 0; q < NKP / 2; ++q) {
+                const ulonglong2 v = cp[q];
+                c[2 * q] = v.x;
+                if (2 * q + 1 < NK) c[2 * q + 1] = v.y;
+            }
+#pragma unroll
+            for (int x3 = 0; x3 < B3 / 2; ++x3) {
+                const ulonglong2 v = wp[x3];
+                wp3[2 * x3] = v.x;
+                wp3[2 * x3 + 1] = v.y;
+            }
 #pragma unroll
             for (int x3 = 0; x3 < B3; ++x3) {
                 if (mask & (1u << x3)) {                 // the same for every lane
