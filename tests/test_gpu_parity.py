@@ -80,9 +80,10 @@ CASES = {
     "fft2_200_250": ((8, 160, 200), 4, 1.25, 2, 2, 4, 1, 300, [0, 1]),
     "fft2_240_256": ((120, 8, 128), 4, 2.0, 1, 1, 3, 1, 200, [0]),
     # channel groups: interpolation runs 32 // W channels per launch (W=6: 5 + 2),
-    # the spread 8 per launch (K=10: 8 + 2, 8-byte column stores)
+    # the spread 8 per launch (K=10: 8 + 2, 8-byte column stores); three coils at
+    # W=4 take interpolation's two-coil gather round and its one-coil tail
     "w6_k7_groups": ((18, 20, 16), 6, 2.0, 7, 2, 9, 1, 300, [1, 0]),
-    "w4_k10_groups": ((16, 16, 16), 4, 1.25, 10, 2, 12, 1, 400, [0, 1]),
+    "w4_k10_groups": ((16, 16, 16), 4, 1.25, 10, 2, 12, 1, 400, [0, 1, 1]),
 }
 
 
