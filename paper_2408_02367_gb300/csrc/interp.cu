@@ -24,7 +24,7 @@
 // window, one load per lane and row (the warp reads one contiguous run per
 // row), weights them by phi1 phi2 (the same in every lane), multiplies by the
 // lane's coefficient and reduces over the warp.  More than 32 / W channels run
-// as several launches, each adding its groups' sum into y.
+// as several launches, each adding its group's sum into y.
 //
 // Tap kernel (nk == 1): lanes own ceil(W^3 / 32) taps each, whose weights and
 // offsets stay in registers across the coils; the W taps of a row are adjacent
