@@ -126,7 +126,12 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *   fft_cols      grid columns per CTA of the strided axis-1 and axis-2 FFT
  *                 passes: 0 (default: 16, or 8 for lengths >= 240), 32 (lengths
  *                 up to 160; longer axes keep the default) or 8.
- *   reserved      must be 0.
+ *   interp_threads  threads per CTA of the persistent interpolation kernel:
+ *                 0 (default: 1024 for W <= 4, else 256), 256 or 1024 (W <= 4
+ *                 only, else SDP_ERR_UNSUPPORTED).  1024 puts one CTA on an SM,
+ *                 whose warps then gather for consecutive samples and share
+ *                 the SM's L1; 256 leaves more registers per thread, so more
+ *                 gathers in flight per warp.
  */
 typedef struct {
     int32_t spread_bins[3];
@@ -134,7 +139,7 @@ typedef struct {
     int32_t fft_engine;
     int32_t fft_lines;
     int32_t fft_cols;
-    int32_t reserved[1];
+    int32_t interp_threads;
 } sdp_tuning;
 
 /*

@@ -43,6 +43,7 @@ struct sdp_plan_s {
     int bs[3] = {0, 0, 0};
     int nb[3] = {0, 0, 0};
     int spread_chunk = 0;
+    int interp_threads = 0;   // resolved CTA size of the interpolation kernel
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -206,6 +207,10 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
         p->ax[a].lines = tn ? tn->fft_lines : 0;
         p->ax[a].cols = tn ? tn->fft_cols : 0;
     }
+    // interpolation CTA size: the 1024-thread kernel is built for W <= 4 only
+    const int ithreads = tn ? tn->interp_threads : 0;
+    if (ithreads == 1024 && W > 4) return SDP_ERR_UNSUPPORTED;
+    p->interp_threads = ithreads ? ithreads : (W <= 4 ? 1024 : 256);
 
     // ---- host tables ----
     std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
@@ -487,8 +492,8 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
         return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3 * nk, B, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk, static_cast<float2*>(y),
-                             accumulate, st);
+        return launch_interp(g, p->interp_threads, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk,
+                             static_cast<float2*>(y), accumulate, st);
     }));
     return SDP_OK;
 }
@@ -620,7 +625,8 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
     if (tn) {
         if (tn->spread_chunk < 32 || tn->spread_chunk > 65536 || tn->fft_engine < 0 || tn->fft_engine > 1 ||
             (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) ||
-            (tn->fft_cols != 0 && tn->fft_cols != 32 && tn->fft_cols != 8) || tn->reserved[0])
+            (tn->fft_cols != 0 && tn->fft_cols != 32 && tn->fft_cols != 8) ||
+            (tn->interp_threads != 0 && tn->interp_threads != 256 && tn->interp_threads != 1024))
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -715,8 +721,8 @@ int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* st
                              p->counters, p->nbins, st);
     }));
     return run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K, static_cast<float2*>(out), 0,
-                             st);
+        return launch_interp(g, p->interp_threads, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K,
+                             static_cast<float2*>(out), 0, st);
     });
 }
 
@@ -769,6 +775,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->fft_engine = p->ax[0].generic;
     out->fft_lines = p->ax[2].lines;
     out->fft_cols = p->ax[0].cols;
+    out->interp_threads = p->interp_threads;
     return SDP_OK;
 }
 

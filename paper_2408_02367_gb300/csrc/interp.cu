@@ -119,15 +119,14 @@ __device__ __forceinline__ void put(float2* __restrict__ dst, float ax, float ay
 // c (NT/32) + w + k gridDim.x (NT/32), k = 0, 1, ...: the whole grid of warps
 // moves through one window of consecutive samples (their windows overlap, so
 // most gathers hit L2), and the warps of a CTA, resident on one SM, take
-// neighbouring samples (their gathers share the SM's L1).  For W <= 4 one
-// 1024-thread CTA fills an SM.  The next sample's coordinates, frame and
+// neighbouring samples (their gathers share the SM's L1).  NT is a plan
+// choice: 1024 (the default for W <= 4: one CTA fills an SM, whose 32 warps
+// take 32 consecutive samples) or 256 (more registers per thread, so more
+// gathers in flight per warp).  The next sample's coordinates, frame and
 // weights are loaded while the current one is interpolated.  For W <= 4 the gathers of two coils are issued together and
 // the two sums share one warp reduction (lanes 0-15 finish coil b, lanes
 // 16-31 coil b + 1).
-template <int W>
-constexpr int rows_threads() { return W <= 4 ? 1024 : 256; }
-
-template <int W, int NT = rows_threads<W>()>
+template <int W, int NT>
 __global__ void __launch_bounds__(NT) interp_rows_kernel(Geo g, const float4* __restrict__ pts,
                                                               const int* __restrict__ tframe,
                                                               const float* __restrict__ wts,
@@ -298,23 +297,15 @@ __global__ void __launch_bounds__(kThreads) interp_taps_kernel(Geo g, const floa
     }
 }
 
-template <int W>
-cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
-                     const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
-    const long long warps_per_block = kThreads / 32;
-    long long nblk = ((long long)g.J + warps_per_block - 1) / warps_per_block;
-    if (nblk > 0x7fffffffLL) nblk = 0x7fffffffLL;
-    constexpr int NT = rows_threads<W>();
-    if (nk == 1) {
-        interp_taps_kernel<W><<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, y,
-                                                                  accumulate);
-        return cudaGetLastError();
-    }
+template <int W, int NT>
+cudaError_t launch_rows(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
+                        const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
     // persistent grid: the CTAs that are resident at once (or fewer for a short trajectory)
     static std::atomic<int> resident{0};
     int per_sm = resident.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_rows_kernel<W>, NT, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_rows_kernel<W, NT>, NT, 0) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         resident.store(per_sm, std::memory_order_relaxed);
@@ -329,13 +320,30 @@ cudaError_t launch_w(const Geo& g, const float4* pts, const int* tframe, const f
     constexpr int kGroup = 32 / W;   // channels per launch
     for (int c0 = 0; c0 < nk; c0 += kGroup) {
         const int cg = nk - c0 < kGroup ? nk - c0 : kGroup;
-        interp_rows_kernel<W><<<nrow, NT, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
-                                                  accumulate || c0 > 0);
+        interp_rows_kernel<W, NT><<<nrow, NT, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
+                                                      accumulate || c0 > 0);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (c0 > 0) note_launches(1);   // the stage counts its first launch
     }
     return cudaSuccess;
+}
+
+template <int W>
+cudaError_t launch_w(const Geo& g, int threads, const float4* pts, const int* tframe, const float* wts,
+                     const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
+                     cudaStream_t st) {
+    if (nk == 1) {
+        const long long warps_per_block = kThreads / 32;
+        long long nblk = ((long long)g.J + warps_per_block - 1) / warps_per_block;
+        if (nblk > 0x7fffffffLL) nblk = 0x7fffffffLL;
+        interp_taps_kernel<W><<<(unsigned)nblk, kThreads, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, y,
+                                                                  accumulate);
+        return cudaGetLastError();
+    }
+    if (W <= 4 && threads == 1024)
+        return launch_rows<W, (W <= 4 ? 1024 : 256)>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+    return launch_rows<W, 256>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
 }
 
 }  // namespace
@@ -348,17 +356,17 @@ cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
-                          const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
+cudaError_t launch_interp(const Geo& g, int threads, const float4* pts, const int* tframe, const float* wts,
+                          const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                           cudaStream_t st) {
     switch (g.W) {
-        case 2: return launch_w<2>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 3: return launch_w<3>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 4: return launch_w<4>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 5: return launch_w<5>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 6: return launch_w<6>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 7: return launch_w<7>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 8: return launch_w<8>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 2: return launch_w<2>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 3: return launch_w<3>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 4: return launch_w<4>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 5: return launch_w<5>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 6: return launch_w<6>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 7: return launch_w<7>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 8: return launch_w<8>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -104,8 +104,7 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({"fft_cols": 16})                                        # 0, 32 or 8 only
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
-    t = op.Tuning.of({})
-    t.reserved[0] = 3
+    t = op.Tuning.of({"interp_threads": 512})                                 # 0, 256 or 1024 only
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})                                                       # valid tuning, no descriptor
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1

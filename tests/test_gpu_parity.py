@@ -145,6 +145,8 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (8, 4, 8), "spread_chunk": 256, "fft_engine": 0, "fft_lines": 4},
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": 32},
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 8},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
+    {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "interp_threads": 1024},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, short spread
@@ -154,12 +156,27 @@ def test_tuned_kernel_shapes_match_oracle(tuning):
     geo = O.Geometry(c["n"], 4, 1.25)
     A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2, tuning=tuning)
     assert A.tuning["spread_bins"] == tuple(tuning["spread_bins"]) and A.tuning["spread_chunk"] == tuning["spread_chunk"]
+    assert A.tuning["interp_threads"] == (tuning.get("interp_threads") or 1024)     # W = 4: 1024 by default
     y = A.forward(t(c["x"]), t(c["coils"])).cpu().numpy()
     assert rel(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"])) < FP32_BOUND
     r = np.ascontiguousarray(y)
     a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
     assert rel(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"])) < FP32_BOUND
     assert A.status() == 0
+
+
+def test_interp_threads_choice_by_width():
+    """1024-thread interpolation CTAs exist for W <= 4 only; wider kernels default to 256."""
+    from paper_2408_02367_gb300 import op
+    c = make_case((12, 12, 12), 6, 2.0, 2, 2, 4, 1, 200, [1, 0])
+    args = (c["omega"], c["frame"], c["n"], 6, 2.0, c["V"], c["S"], 2)
+    with pytest.raises(op.SdpError):
+        op.make_operator(*args, tuning={"interp_threads": 1024})
+    assert op.make_operator(*args).tuning["interp_threads"] == 256
+    A = op.make_operator(*args, tuning={"interp_threads": 256})
+    y = A.forward(t(c["x"]), t(c["coils"])).cpu().numpy()
+    geo = O.Geometry(c["n"], 6, 2.0)
+    assert rel(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"])) < FP32_BOUND
 
 
 def test_autotuner_candidates_agree_and_cache(tmp_path):
