@@ -207,104 +207,193 @@ __global__ void __launch_bounds__(kThreads, 4) tv_value_kernel(const float2* __r
     finish_value(block_sum_f(acc, red), lambda, partials, counter, out, red);
 }
 
-// The loads of one step of the gradient kernel: x(p+1, i2, i3), x(p, i2+1, i3),
-// x(p+1, i2-1, i3); in the last lane x(p, i2, i3+1) and x(p, i2-1, i3+1); in
-// lane 0 x(p+1, i2, i3-1) and x(p, i2+1, i3-1).
-struct StepG {
-    float2 b, dn, ub, rt, urt, lfb, lfd;
+// Gradient kernel: a thread owns two rows of its column, A = y0 + 2w and
+// B = A + 1 (warp w of 4; the block still covers a TX x TY tile).  Row B's
+// "point above" is row A, so q_2 of the point above B is row A's own q_2, and
+// x(p, B) is row A's axis-2 neighbour: per plane the pair needs x(p+1, A),
+// x(p+1, B), x(p, B+1) and x(p+1, A-1) (in the last lane also x(p, A, i3+1),
+// x(p, B, i3+1), x(p, A-1, i3+1); in lane 0 x(p+1, A, i3-1), x(p+1, B, i3-1),
+// x(p, B+1, i3-1)).
+constexpr int kThreadsG = TX * TY / 2;
+constexpr int PFG = 3;             // planes of loads in flight per thread (10 values per plane)
+
+struct Offs2 {
+    int a, b, bd, au;              // rows A, B, B + 1, A - 1 at column i3
+    int rta, rtb, urt;             // column i3 + 1 of rows A, B, A - 1
+    int lfa, lfb, lfbd;            // column i3 - 1 of rows A, B, B + 1
+    bool up_a, dn_a, dn_b, rt, lf; // the neighbour lies on the volume
 };
 
-__device__ __forceinline__ StepG load_g(const float2* __restrict__ xk, const Vol& v, const Offs& o, int p,
-                                        bool first_lane, bool last_lane) {
+__device__ __forceinline__ Offs2 offsets2_of(const Vol& v, int ia, int i3) {
+    Offs2 o;
+    auto row = [&](int r) { return min(max(r, 0), v.N2 - 1) * v.N3; };
+    const int c0 = min(i3, v.N3 - 1);
+    const int crt = min(c0 + 1, v.N3 - 1), clf = max(c0 - 1, 0);
+    const int ra = row(ia), rb = row(ia + 1), rbd = row(ia + 2), rau = row(ia - 1);
+    o.a = ra + c0;
+    o.b = rb + c0;
+    o.bd = rbd + c0;
+    o.au = rau + c0;
+    o.rta = ra + crt;
+    o.rtb = rb + crt;
+    o.urt = rau + crt;
+    o.lfa = ra + clf;
+    o.lfb = rb + clf;
+    o.lfbd = rbd + clf;
+    o.up_a = ia > 0;
+    o.dn_a = ia + 1 < v.N2;
+    o.dn_b = ia + 2 < v.N2;
+    o.rt = i3 + 1 < v.N3;
+    o.lf = i3 > 0;
+    return o;
+}
+
+struct StepG2 {
+    float2 ba, bb, dnb, ub;        // x(p+1, A), x(p+1, B), x(p, B+1), x(p+1, A-1)
+    float2 rta, rtb, urt;          // last lane
+    float2 lfba, lfbb, lfdb;       // lane 0
+};
+
+__device__ __forceinline__ StepG2 load_g2(const float2* __restrict__ xk, const Vol& v, const Offs2& o, int p,
+                                          bool first_lane, bool last_lane) {
     const int pc = min(p, v.N1 - 1) * (int)v.plane, pn = min(p + 1, v.N1 - 1) * (int)v.plane;
     const float2 z = make_float2(0.f, 0.f);
-    StepG r;
-    r.b = ldx(xk + pn + o.o0);
-    r.dn = ldx(xk + pc + o.dn);
-    r.ub = ldx(xk + pn + o.up);
-    r.rt = last_lane ? ldx(xk + pc + o.rt) : z;
+    StepG2 r;
+    r.ba = ldx(xk + pn + o.a);
+    r.bb = ldx(xk + pn + o.b);
+    r.dnb = ldx(xk + pc + o.bd);
+    r.ub = ldx(xk + pn + o.au);
+    r.rta = last_lane ? ldx(xk + pc + o.rta) : z;
+    r.rtb = last_lane ? ldx(xk + pc + o.rtb) : z;
     r.urt = last_lane ? ldx(xk + pc + o.urt) : z;
-    r.lfb = first_lane ? ldx(xk + pn + o.lf) : z;
-    r.lfd = first_lane ? ldx(xk + pc + o.dnlf) : z;
+    r.lfba = first_lane ? ldx(xk + pn + o.lfa) : z;
+    r.lfbb = first_lane ? ldx(xk + pn + o.lfb) : z;
+    r.lfdb = first_lane ? ldx(xk + pc + o.lfbd) : z;
     return r;
 }
 
-// gradient: out = (accumulate ? out : 0) + lambda * (*scale) * grad TV.  Besides
-// its own q_d, a thread forms q_2 of the point above it (i2 - 1) from that
-// row's values, and takes q_3 of the point left of it (i3 - 1) from the lane
-// to its left (lane 0 forms it from the column left of the tile); q_1 of the
-// plane before is the register kept from the previous step (a warm-up step at
-// pb - 1 supplies it).
-__global__ void __launch_bounds__(kThreads, 2) tv_grad_kernel(const float2* __restrict__ x, Vol v, float eps,
-                                                             float lambda, const float* __restrict__ scale,
-                                                             float2* __restrict__ out, int accumulate) {
-    const Col c = column_of(v);
-    const Offs o = offsets_of(v, c);
+// q = D x / s at one point from its three forward differences.
+__device__ __forceinline__ void qvec(float2 d1, float2 d2, float2 d3, float eps2, float2& q1, float2& q2, float2& q3) {
+    const float is = rsqrtf(smag2(d1, d2, d3, eps2));              // 1 / s (hardware rsqrt)
+    q1 = scl(d1, is);
+    q2 = scl(d2, is);
+    q3 = scl(d3, is);
+}
+
+// gradient: out = (accumulate ? out : 0) + lambda * (*scale) * grad TV.  q_1 of
+// the plane before is the register kept from the previous step (a warm-up step
+// at pb - 1 supplies it); q_3 of the point to the left comes from the lane to
+// the left (lane 0 forms it from the column left of the tile); q_2 of the point
+// above row A is formed from row A - 1's values, that of row B is row A's.
+__global__ void __launch_bounds__(kThreadsG, 4) tv_grad_kernel(const float2* __restrict__ x, Vol v, float eps,
+                                                              float lambda, const float* __restrict__ scale,
+                                                              float2* __restrict__ out, int accumulate) {
+    int bi = blockIdx.x;
+    const int t3 = bi % v.nt3;
+    bi /= v.nt3;
+    const int t2 = bi % v.nt2;
+    const int sg = bi / v.nt2;
+    const int lane = threadIdx.x & 31;
+    const int i3 = t3 * TX + lane;
+    const int ia = t2 * TY + 2 * (threadIdx.x >> 5);
+    const int pb = sg * SEG, pe = min(v.N1, pb + SEG);
+    const bool in_a = ia < v.N2 && i3 < v.N3, in_b = ia + 1 < v.N2 && i3 < v.N3;
+    const Offs2 o = offsets2_of(v, ia, i3);
     const float eps2 = eps * eps;
     const float f = lambda * (scale ? __ldg(scale) : 1.f);
     const float2 z = make_float2(0.f, 0.f);
-    const float2* xk = x + (long long)c.k * v.nvox;
-    float2* ok = out + (long long)c.k * v.nvox;
+    const float2* xk = x + (long long)blockIdx.y * v.nvox;
+    float2* ok = out + (long long)blockIdx.y * v.nvox;
     const int plane = (int)v.plane;
-    const bool first_lane = c.lane == 0, last_lane = c.lane == 31;
-    const int p0 = c.pb > 0 ? c.pb - 1 : 0;
-    float2 a = ldx(xk + p0 * plane + o.o0);                          // x(p, i2, i3)
-    float2 up = ldx(xk + p0 * plane + o.up);                         // x(p, i2 - 1, i3)
-    float2 lf = first_lane ? ldx(xk + p0 * plane + o.lf) : z;        // x(p, i2, i3 - 1), lane 0
-    StepG q[PF];
+    const bool first_lane = lane == 0, last_lane = lane == 31;
+    const int p0 = pb > 0 ? pb - 1 : 0;
+    float2 xa = ldx(xk + p0 * plane + o.a);                          // x(p, A)
+    float2 xb = ldx(xk + p0 * plane + o.b);                          // x(p, B)
+    float2 up = ldx(xk + p0 * plane + o.au);                         // x(p, A - 1)
+    float2 lfa = first_lane ? ldx(xk + p0 * plane + o.lfa) : z;      // x(p, A, i3 - 1), lane 0
+    float2 lfb = first_lane ? ldx(xk + p0 * plane + o.lfb) : z;      // x(p, B, i3 - 1), lane 0
+    StepG2 q[PFG];
 #pragma unroll
-    for (int j = 0; j < PF; ++j) q[j] = load_g(xk, v, o, p0 + j, first_lane, last_lane);
-    float2 q1p = z;                                                  // q_1(p - 1, i2, i3)
+    for (int j = 0; j < PFG; ++j) q[j] = load_g2(xk, v, o, p0 + j, first_lane, last_lane);
+    float2 q1pa = z, q1pb = z;                                       // q_1 of the plane before
 #pragma unroll
     for (int j = 0; j <= SEG; ++j) {
         const int p = p0 + j;
-        StepG cur = q[j % PF];
-        if (j + PF <= SEG) q[j % PF] = load_g(xk, v, o, p + PF, first_lane, last_lane);
-        const float2 sr = shfl_down1(a), sur = shfl_down1(up);
+        StepG2 cur = q[j % PFG];
+        if (j + PFG <= SEG) q[j % PFG] = load_g2(xk, v, o, p + PFG, first_lane, last_lane);
+        const float2 sra = shfl_down1(xa), srb = shfl_down1(xb), sru = shfl_down1(up);
         if (!last_lane) {
-            cur.rt = sr;
-            cur.urt = sur;
+            cur.rta = sra;
+            cur.rtb = srb;
+            cur.urt = sru;
         }
-        if (p + 1 >= v.N1) {
-            cur.b = a;
+        if (p + 1 >= v.N1) {                                         // no plane after: D1 = 0
+            cur.ba = xa;
+            cur.bb = xb;
             cur.ub = up;
-            cur.lfb = lf;
+            cur.lfba = lfa;
+            cur.lfbb = lfb;
         }
-        if (!o.has_dn) {
-            cur.dn = a;
-            cur.lfd = lf;
-        }
-        if (!o.has_rt) {
-            cur.rt = a;
+        if (!o.rt) {
+            cur.rta = xa;
+            cur.rtb = xb;
             cur.urt = up;
         }
-        const float2 d1 = sub(cur.b, a), d2 = sub(cur.dn, a), d3 = sub(cur.rt, a);
-        const float is = rsqrtf(smag2(d1, d2, d3, eps2));           // 1 / s (hardware rsqrt)
-        const float2 q1 = scl(d1, is), q2 = scl(d2, is), q3 = scl(d3, is);
-        const float2 e2 = sub(a, up);                                // q_2(p, i2 - 1, i3)
-        float2 q2u = scl(e2, rsqrtf(smag2(sub(cur.ub, up), e2, sub(cur.urt, up), eps2)));
-        if (!o.has_up) q2u = z;
-        float2 q3l = shfl_up1(q3);                                   // q_3(p, i2, i3 - 1)
+        const float2 dna = o.dn_a ? xb : xa;                          // x(p, A+1) or no difference
+        const float2 lfda = o.dn_a ? lfb : lfa;
+        if (!o.dn_b) {
+            cur.dnb = xb;
+            cur.lfdb = lfb;
+        }
+        float2 q1a, q2a, q3a, q1b, q2b, q3b;
+        qvec(sub(cur.ba, xa), sub(dna, xa), sub(cur.rta, xa), eps2, q1a, q2a, q3a);
+        qvec(sub(cur.bb, xb), sub(cur.dnb, xb), sub(cur.rtb, xb), eps2, q1b, q2b, q3b);
+        // q_2 of the point above row A (0 off the volume)
+        const float2 e2 = sub(xa, up);
+        float2 q2ua = scl(e2, rsqrtf(smag2(sub(cur.ub, up), e2, sub(cur.urt, up), eps2)));
+        if (!o.up_a) q2ua = z;
+        // q_3 of the points to the left (0 off the volume)
+        float2 q3la = shfl_up1(q3a), q3lb = shfl_up1(q3b);
         if (first_lane) {
-            const float2 g3 = sub(a, lf);
-            q3l = scl(g3, rsqrtf(smag2(sub(cur.lfb, lf), sub(cur.lfd, lf), g3, eps2)));
+            const float2 ga = sub(xa, lfa), gb = sub(xb, lfb);
+            q3la = scl(ga, rsqrtf(smag2(sub(cur.lfba, lfa), sub(lfda, lfa), ga, eps2)));
+            q3lb = scl(gb, rsqrtf(smag2(sub(cur.lfbb, lfb), sub(cur.lfdb, lfb), gb, eps2)));
         }
-        if (!o.has_lf) q3l = z;
-        if (c.inside && p >= c.pb && p < c.pe) {
-            float2 g = make_float2(f * (q1p.x - q1.x + q2u.x - q2.x + q3l.x - q3.x),
-                                   f * (q1p.y - q1.y + q2u.y - q2.y + q3l.y - q3.y));
-            float2* dst = ok + p * plane + o.o0;
-            if (accumulate) {
-                const float2 prev = *dst;
-                g.x += prev.x;
-                g.y += prev.y;
+        if (!o.lf) {
+            q3la = z;
+            q3lb = z;
+        }
+        if (p >= pb && p < pe) {
+            float2* dst = ok + p * plane + o.a;
+            if (in_a) {
+                float2 g = make_float2(f * (q1pa.x - q1a.x + q2ua.x - q2a.x + q3la.x - q3a.x),
+                                       f * (q1pa.y - q1a.y + q2ua.y - q2a.y + q3la.y - q3a.y));
+                if (accumulate) {
+                    const float2 prev = *dst;
+                    g.x += prev.x;
+                    g.y += prev.y;
+                }
+                *dst = g;
             }
-            *dst = g;
+            if (in_b) {
+                float2* dstb = dst + v.N3;
+                float2 g = make_float2(f * (q1pb.x - q1b.x + q2a.x - q2b.x + q3lb.x - q3b.x),
+                                       f * (q1pb.y - q1b.y + q2a.y - q2b.y + q3lb.y - q3b.y));
+                if (accumulate) {
+                    const float2 prev = *dstb;
+                    g.x += prev.x;
+                    g.y += prev.y;
+                }
+                *dstb = g;
+            }
         }
-        q1p = q1;
-        a = cur.b;
+        q1pa = q1a;
+        q1pb = q1b;
+        xa = cur.ba;
+        xb = cur.bb;
         up = cur.ub;
-        lf = cur.lfb;
+        lfa = cur.lfba;
+        lfb = cur.lfbb;
     }
 }
 
@@ -341,7 +430,7 @@ cudaError_t launch_tv_grad(const Geo& g, const float2* x, float eps, float lambd
     const Vol v = make_vol(g);
     if (v.nvox >= (1LL << 31)) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)(v.nt3 * v.nt2 * v.nseg), (unsigned)g.K);
-    tv_grad_kernel<<<grid, kThreads, 0, st>>>(x, v, eps, lambda, scale, out, accumulate);
+    tv_grad_kernel<<<grid, kThreadsG, 0, st>>>(x, v, eps, lambda, scale, out, accumulate);
     return cudaGetLastError();
 }
 
