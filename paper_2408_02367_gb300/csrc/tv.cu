@@ -10,8 +10,9 @@
 // grad is dTV/dRe + i dTV/dIm (PyTorch's convention).
 //
 // Both kernels march along axis 1.  A block owns a TY x TX tile of (i2, i3)
-// for one channel and a segment of SEG planes; warp w of the block holds row
-// i2 = y0 + w, lane l holds i3 = x0 + l, and every thread walks its column
+// for one channel and a segment of SEG planes; in the value kernel warp w of
+// the block holds row i2 = y0 + w (in the gradient kernel rows y0 + 2w and
+// y0 + 2w + 1), lane l holds i3 = x0 + l, and every thread walks its column
 // (i2, i3) plane by plane.  The axis-3 neighbours come from warp shuffles
 // (the last lane loads the one past the tile), the axis-2 neighbours are
 // loads of the neighbouring rows (hits in L1 or L2: those rows are another
