@@ -388,17 +388,18 @@ def run_native(args):
             A.profile(True)
             A.profile_read()
         n0 = op.launch_count()
-        # the timed DIP steps run between cudaProfilerStart/Stop (no-ops without a
-        # profiler), so `ncu --profile-from-start off` lists exactly their launches,
-        # backward included (autograd launches it from its own thread)
-        if label == "dip_step":
+        # with --profile-range the timed DIP steps run between cudaProfilerStart/Stop
+        # (no-ops without a profiler), so `ncu --profile-from-start off` lists exactly
+        # their launches, backward included (autograd launches it from its own thread)
+        bracket = label == "dip_step" and args.profile_range
+        if bracket:
             torch.cuda.profiler.start()
         for i in range(steps):
             flush.fill_(float(i))                # L2 flush, outside the events
             evs[i][0].record()
             fn(coil_dev[start_index + i])
             evs[i][1].record()
-        if label == "dip_step":
+        if bracket:
             torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         launches = op.launch_count() - n0
@@ -678,6 +679,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default kernel shapes instead of the autotuner's")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed DIP steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
