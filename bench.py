@@ -181,7 +181,6 @@ def stage_bytes(w, B, M, ninc):
 # spread, its bin shape): a kernel whose source has changed since reports null.
 NCU_TRAFFIC = {
     ("spread", (8, 4, 4)): ("spread_impl.cuh", "4c832e4000ce8fa9", (95.680000 + 285.588480) * 1e6),
-    "interp": ("interp.cu", "f05f469037122449", (223.855104 + 7.868160) * 1e6),
     "fwd_prologue_fft3": ("fft2.cu", "c0674c266053743b", (117.543936 + 153.601536) * 1e6),
     "adj_ifft3_epilogue": ("fft2.cu", "c0674c266053743b", (243.318528 + 62.533888) * 1e6),
 }
