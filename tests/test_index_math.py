@@ -5,7 +5,9 @@ many shapes, so that an edit can be read against them before it runs on a
 GPU: every element is written exactly once and every index stays in its
 buffer.  The mappings are restated from their definitions in the kernels'
 comments (csrc/spread_impl.cuh store_bin, csrc/interp.cu interp_rows_kernel,
-csrc/fft2.cu fft2_fwd_prologue_kernel); nothing here is method arithmetic.
+csrc/fft2.cu fft2_fwd_prologue_kernel and fft2_adj_epilogue_kernel, csrc/fft.cu
+fwd_prologue_fft3_kernel and adj_fft3_epilogue_kernel); nothing here is method
+arithmetic.
 """
 import itertools
 
@@ -97,6 +99,56 @@ def test_prologue_interleaved_stores_cover_the_lines_once(A, B, NLT, nk):
             row, kk = divmod(gl, nk)
             for q2 in range(B):
                 idx = (row * L + q1 + A * q2) * nk + kk
+                assert 0 <= idx < nrows * L * nk
+                hits[idx] = hits.get(idx, 0) + 1
+    assert len(hits) == nrows * L * nk and all(v == 1 for v in hits.values())
+
+
+@pytest.mark.parametrize("A,B,NLT", [(16, 10, 8), (16, 10, 16), (16, 10, 4), (8, 6, 8), (25, 10, 8)])
+@pytest.mark.parametrize("nk", [1, 2, 5, 8])
+def test_epilogue_interleaved_loads_cover_the_lines_once(A, B, NLT, nk):
+    """Pass 1 of the fused adjoint kernel: thread (l1 = tid % NLT, b1 = tid / NLT)
+    loads FFT positions B a + b1 of line l0 + l1 from a running pointer that
+    starts at ((row L + b1) nk + kk) and steps by B nk."""
+    L = A * B
+    nrows = 6
+    nlines = nrows * nk
+    hits = {}
+    for l0 in range(0, nlines, NLT):
+        for tid in range(NLT * max(A, B)):
+            if tid >= NLT * B:
+                continue
+            l1, b1 = tid % NLT, tid // NLT
+            gl = l0 + l1
+            if gl >= nlines:
+                continue
+            row, kk = divmod(gl, nk)
+            idx = (row * L + b1) * nk + kk
+            for a in range(A):
+                assert 0 <= idx < nrows * L * nk and (idx - kk) // nk % B == b1
+                hits[idx] = hits.get(idx, 0) + 1
+                idx += B * nk
+    assert len(hits) == nrows * L * nk and all(v == 1 for v in hits.values())
+
+
+@pytest.mark.parametrize("L", [48, 81, 150, 160])
+@pytest.mark.parametrize("nk", [1, 5, 16])
+def test_stockham_axis3_interleaved_loops_cover_the_lines_once(L, nk):
+    """Store loop of the Stockham forward prologue and load loop of its adjoint
+    epilogue: e -> (p = e / NL, l = e % NL), grid index ((row L + p) nk + kk)."""
+    NL, threads = 16, 256
+    nrows = 5
+    nlines = nrows * nk
+    hits = {}
+    for l0 in range(0, nlines, NL):
+        for t in range(threads):
+            for e in range(t, NL * L, threads):
+                p, l = divmod(e, NL)
+                gl = l0 + l
+                if gl >= nlines:
+                    continue
+                row, kk = divmod(gl, nk)
+                idx = (row * L + p) * nk + kk
                 assert 0 <= idx < nrows * L * nk
                 hits[idx] = hits.get(idx, 0) + 1
     assert len(hits) == nrows * L * nk and all(v == 1 for v in hits.values())
