@@ -13,8 +13,15 @@ frames of one 1024-sample golden-angle 3D spiral arm (J=491,520 samples per
 coil), Kaiser-Bessel W=4 on a 1.25x oversampled grid (160^3), B=2 coils per
 step.  Synthetic seeded inputs (phantom, coil maps, trajectory, V).
 
-Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
-a bounded sample of the same workload instead.
+Beside the headline step the line carries the whole-brain rows (200x200x160,
+C=32, J=2,048,000: the captured DIP step at coil minibatches 1, 2, 4 and 8, and
+a work list of those four minibatches through the batched calls) and the
+six-volume batch (64^3 .. 200x200x160, one DIP step of every volume in one
+captured batch, plus the full-coil variant against a 150 GB device-memory
+bound).
+
+Prints ONE JSON line (rank 0).  `--impl reference` instead times whole steps of
+the FP64 CPU oracle on the same workload, on every host core.
 """
 from __future__ import annotations
 
@@ -211,89 +218,412 @@ def path_model_bytes(w, B, M):
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle (baseline / reference arm)
+# CPU oracle (baseline / reference arm): whole steps on every host core
 # ----------------------------------------------------------------------------
+#
+# One step of the oracle is the step the GPU times: the forward operator of B
+# coils over all K channels, the residual, and the adjoint of 2r over the same
+# coils and channels.  The oracle's own step functions (A1-A3, A5-A7, FP64
+# numpy) run unchanged; the B*K (coil, channel) pieces of each direction are
+# independent, so they run side by side in a pool of spawned processes, one per
+# piece, up to the host's core count.  Nothing is sampled or scaled: the value
+# is B*J samples over the wall time of whole steps.
 
-def oracle_sample_step(w, problem, geo, coil, k, frames, O):
-    """One coil, one channel, a contiguous block of frames: the six oracle steps timed.
-
-    Returns (t_grid_steps, t_sample_steps, n_samples): the deapod/FFT steps cost
-    the same for any sample count, the interpolation/spread steps scale with it."""
-    x, S, V, omega, frame = problem
-    sel = (frame >= frames[0]) & (frame < frames[1])
-    om = omega[sel]
-    fr = frame[sel]
-    g32 = O.grid_coords(om, geo.M)
-    t0 = time.perf_counter()
-    U = O.fwd_fft(O.fwd_prologue(geo, x[k], S[coil]))
-    t1 = time.perf_counter()
-    yk = O.fwd_interp(geo, U[None], V[:, k:k + 1], g32, fr)
-    t2 = time.perf_counter()
-    H = O.adj_spread(geo, yk, V[:, k:k + 1], g32, fr)
-    t3 = time.perf_counter()
-    O.adj_epilogue(geo, O.adj_ifft(H[0]), S[coil])
-    t4 = time.perf_counter()
-    return (t1 - t0) + (t4 - t3), (t2 - t1) + (t3 - t2), int(sel.sum())
+_ORACLE = {}
 
 
-def oracle_step_seconds(w, B, tg, ts, ns):
-    """Oracle seconds for a whole step: B coils x K channels, all J samples."""
-    return B * w.K * (tg + ts * (w.J / ns))
+def _oracle_init(n, W, sigma, x, S, V, omega, frame):
+    from oracle import nufft as O
+    _ORACLE.update(O=O, geo=O.Geometry(n, W, sigma), x=x, S=S, V=V, omega=omega, frame=frame)
+
+
+def _oracle_fwd(coil, k):
+    """Channel k of A_c(x): A1 prologue, A2 FFT, A3 interpolation with V[:, k]."""
+    d = _ORACLE
+    O, geo = d["O"], d["geo"]
+    g32 = O.grid_coords(d["omega"], geo.M)
+    U = O.fwd_fft(O.fwd_prologue(geo, d["x"][k], d["S"][coil]))
+    return O.fwd_interp(geo, U[None], d["V"][:, k:k + 1], g32, d["frame"])
+
+
+def _oracle_adj(coil, k, r):
+    """Channel k of A_c^H r: A5 spread with conj(V[:, k]), A6 inverse FFT, A7 epilogue."""
+    d = _ORACLE
+    O, geo = d["O"], d["geo"]
+    g32 = O.grid_coords(d["omega"], geo.M)
+    H = O.adj_spread(geo, r, d["V"][:, k:k + 1], g32, d["frame"])
+    out = O.adj_epilogue(geo, O.adj_ifft(H[0]), d["S"][coil])
+    return complex(np.sum(out))      # the image stays in the worker; its sum proves it was formed
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OracleSteps:
+    """Whole oracle steps of one workload (coils drawn like the GPU arm's) on a spawned process pool."""
+
+    def __init__(self, w, B, coils_of_step=None, max_workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.w, self.B = w, B
+        x, S, V, omega, frame = synth.make_problem(w)
+        self.C = w.C
+        self.coils_of_step = coils_of_step
+        self.y_meas = synth.complex_noise((w.C, w.J), 1.0).astype(np.complex128)
+        self.workers = min(B * w.K, os.cpu_count() or 1) if max_workers is None else max_workers
+        self.pool = cf.ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"), initializer=_oracle_init,
+                                           initargs=(w.n, w.width, w.oversamp, x, S, V, omega, frame))
+
+    def step(self, coils):
+        K = self.w.K
+        fut = [[self.pool.submit(_oracle_fwd, int(c), k) for k in range(K)] for c in coils]
+        ys = [sum(f.result() for f in row) for row in fut]                       # A_c(x) of every coil
+        r2 = [2.0 * (y - self.y_meas[int(c)]) for y, c in zip(ys, coils)]        # dL/dyhat (Eq. 3, DCF = 1)
+        loss = float(sum(np.sum(np.abs(0.5 * r) ** 2) for r in r2))
+        fut = [self.pool.submit(_oracle_adj, int(c), k, r) for c, r in zip(coils, r2) for k in range(K)]
+        chk = sum(f.result() for f in fut)
+        return loss, chk
+
+    def time_steps(self, draws):
+        ts = []
+        for coils in draws:
+            t0 = time.perf_counter()
+            self.step(coils)
+            ts.append(time.perf_counter() - t0)
+        return ts
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+
+
+def oracle_line(w, B, ts, workers, what):
+    t = float(np.mean(ts))
+    return {"value": B * w.J / t, "unit": UNIT, "cores": workers, "kind": "oracle", "host_cpus": os.cpu_count(),
+            "cpu_model": cpu_model(), "seconds_per_step": t, "steps_timed": len(ts),
+            "sample": (f"{what}: {len(ts)} whole oracle step(s) of {workload_desc(w, B)}: FP64 numpy forward of "
+                       f"B={B} coils x K={w.K} channels, residual, adjoint of 2r; the B*K (coil, channel) pieces of "
+                       f"each direction run in {workers} spawned processes; nothing scaled")}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import nufft as O
     w = synth.WORKLOADS[args.workload]
-    B = w.batch
-    problem = synth.make_problem(w)
-    geo = O.Geometry(w.n, w.width, w.oversamp)
-    frames = (0, max(1, w.T // 16))
-    rng = np.random.default_rng(rank_seed(synth.SEED_COILS_DRAW, rank))
-    times = []
-    for i in range(args.warmup + args.steps):
-        coil = int(rng.integers(0, w.C))
-        k = i % w.K
-        tg, ts, ns = oracle_sample_step(w, problem, geo, coil, k, frames, O)
-        if i >= args.warmup:
-            times.append(oracle_step_seconds(w, B, tg, ts, ns))
-    t = float(np.mean(times))
-    value = B * w.J / t
-    sample = (f"per step: FP64 oracle (numpy, 1 thread) forward+adjoint of 1 coil x 1 channel on the full "
-              f"{geo.M[0]}x{geo.M[1]}x{geo.M[2]} grid with frames {frames[0]}..{frames[1] - 1} "
-              f"({ns} samples); time scaled to B*K coil-channels and J samples per coil")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+    B = args.batch or w.batch
+    draws = synth.coil_minibatches(w.C, B, args.warmup + args.steps, seed=rank_seed(synth.SEED_COILS_DRAW, rank))
+    t_start = time.perf_counter()
+    orc = OracleSteps(w, B)
+    try:
+        orc.time_steps(draws[:args.warmup])
+        ts = orc.time_steps(draws[args.warmup:])
+    finally:
+        orc.close()
+    base = oracle_line(w, B, ts, orc.workers, "per step")
+    t = base["seconds_per_step"]
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(w, B), "parallelism": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                             "host_cpus": os.cpu_count()},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": workload_desc(w, B), "parallelism": f"cpu, {orc.workers} processes"},
+            "cpu_baseline": base, "run_seconds": time.perf_counter() - t_start,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def cpu_baseline(w, B, budget_s=20.0):
-    from oracle import nufft as O
-    problem = synth.make_problem(w)
-    geo = O.Geometry(w.n, w.width, w.oversamp)
-    frames = (0, max(1, w.T // 4))
-    t_start = time.perf_counter()
-    ests = []
-    k = 0
-    while not ests or (time.perf_counter() - t_start < budget_s and len(ests) < 4):
-        tg, ts, ns = oracle_sample_step(w, problem, geo, 1, k % w.K, frames, O)
-        ests.append(oracle_step_seconds(w, B, tg, ts, ns))
-        k += 1
-    t = float(np.median(ests))
-    return {"value": B * w.J / t, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cpus": os.cpu_count(),
-            "sample": (f"{len(ests)} runs of the FP64 oracle (numpy, 1 thread) forward+adjoint for 1 coil x 1 "
-                       f"channel on the full {geo.M[0]}x{geo.M[1]}x{geo.M[2]} grid with frames "
-                       f"{frames[0]}..{frames[1] - 1} ({ns} samples), scaled to B*K coil-channels and J "
-                       f"samples per coil; median"),
-            "seconds_per_step": t}
+def cpu_baseline(w, B, whole_brain=False):
+    """The oracle on the host cores: whole steps of the bench workload (the reported value), of the
+    32^3 W=6 workload, and with whole_brain one coil x all K of the 200x200x160 workload."""
+    draws = synth.coil_minibatches(w.C, B, 3, seed=synth.SEED_COILS_DRAW + 77)
+    orc = OracleSteps(w, B)
+    try:
+        orc.time_steps(draws[:1])                 # starts the workers
+        ts = orc.time_steps(draws[1:])
+    finally:
+        orc.close()
+    out = oracle_line(w, B, ts, orc.workers, "bench workload")
+    rows = {}
+    w1 = synth.WORKLOADS["vol32_w6"]
+    orc = OracleSteps(w1, w1.batch)
+    try:
+        coils = [np.arange(w1.batch)] * 3
+        orc.time_steps(coils[:1])
+        rows["vol32_w6"] = oracle_line(w1, w1.batch, orc.time_steps(coils[1:]), orc.workers, "32^3 workload")
+    finally:
+        orc.close()
+    if whole_brain:
+        w4 = synth.WORKLOADS["vol200_w4"]
+        orc = OracleSteps(w4, 1)
+        try:
+            rows["vol200_w4_one_coil"] = oracle_line(w4, 1, orc.time_steps([np.array([0])]), orc.workers,
+                                                     "whole-brain workload, one coil")
+        finally:
+            orc.close()
+    out["other_workloads"] = rows
+    return out
+
+
+# ----------------------------------------------------------------------------
+# whole-brain and multi-volume rows (measured beside the headline step)
+# ----------------------------------------------------------------------------
+
+def _upload_plan(op, torch, w, omega, frame, V, S, max_batch, dev, tuning):
+    """Inputs to the device first, then the plan alone timed (sdp_plan_create: host grid coordinates,
+    bin sort and incidence lists, device tables, the coil-map copy)."""
+    traj = torch.from_numpy(np.ascontiguousarray(omega, np.float32)).to(dev)
+    Vt = torch.from_numpy(np.ascontiguousarray(V, np.complex64)).to(dev)
+    St = torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev)
+    off = np.searchsorted(np.asarray(frame), np.arange(w.T + 1), side="left").astype(np.int64)
+    off[-1] = len(frame)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    A = op.SubspaceNufft(traj, off, w.n, w.width, w.oversamp, Vt, St, max_batch=max_batch, tuning=tuning)
+    torch.cuda.synchronize(dev)
+    return A, time.perf_counter() - t0
+
+
+def _measured_kspace(A, torch, x_true, C, dev, maxB):
+    """y_c = A_c(x_true) + complex noise at 30 dB SNR for every coil, in minibatches of maxB."""
+    xt = torch.from_numpy(x_true).to(dev)
+    y = torch.empty((C, A.J), dtype=torch.complex64, device=dev)
+    for c0 in range(0, C, maxB):
+        c1 = min(C, c0 + maxB)
+        A.forward(xt, torch.arange(c0, c1, dtype=torch.int32, device=dev), out=y[c0:c1])
+    sig = float(torch.linalg.norm(y).item()) ** 2 / (y.numel() * 1e3)
+    y += torch.from_numpy(synth.complex_noise((C, A.J), math.sqrt(sig))).to(dev)
+    return y
+
+
+def _events_ms(torch, fn, n, flush, per_call_args=None):
+    """Mean CUDA-event time of n calls, L2 flushed before each (outside the events)."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for i in range(n):
+        flush.fill_(float(i))
+        evs[i][0].record()
+        fn(i)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / n
+
+
+def _plain_step(A, torch, x, y_meas, ci, K):
+    """The plain form: one coil and one channel per launch, same arithmetic."""
+    B = ci.numel()
+    y_p = torch.zeros((B, A.J), dtype=torch.complex64, device=x.device)
+    for b in range(B):
+        for k in range(K):
+            A.forward(x, ci[b:b + 1], out=y_p[b:b + 1], k0=k, nk=1, accumulate=True)
+    r2, loss = A.residual_loss(y_p, y_meas, ci)
+    g = torch.zeros_like(x)
+    for b in range(B):
+        for k in range(K):
+            A.adjoint(r2[b:b + 1].contiguous(), ci[b:b + 1], out=g, accumulate=True, k0=k, nk=1)
+    return y_p, loss, g
+
+
+def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
+    """200x200x160, C=32, J=2,048,000: the graph-captured DIP step at each coil minibatch B in {1,2,4,8}
+    (against the plain form at equal accuracy), and the work list of four items (own TSMI each, B=1,2,4,8)
+    through one batched forward and one batched adjoint."""
+    from paper_2408_02367_gb300 import graph as sdp_graph
+    w = synth.WORKLOADS["vol200_w4"]
+    Bmax = max(synth.WHOLE_BRAIN_BATCHES)
+    t0 = time.perf_counter()
+    x_true, S, V, omega, frame = synth.make_problem(w)
+    synth_s = time.perf_counter() - t0
+    A, plan_s = _upload_plan(op, torch, w, omega, frame, V, S, Bmax, dev, tuning)
+    del S
+    info = A.info()
+    M = (info["M1"], info["M2"], info["M3"])
+    y_meas = _measured_kspace(A, torch, x_true, w.C, dev, Bmax)
+    x_hat = torch.from_numpy(synth.ellipsoid_phantom(w.n, w.K, seed=1)).to(dev)
+    nsteps = min(args.steps, 20)
+    rows = {"workload": workload_desc(w, Bmax).replace(f", coil minibatch B={Bmax}", ""), "grid": list(M),
+            "plan_create_s": plan_s, "synth_inputs_s": synth_s, "plan_device_bytes": info["total_bytes"],
+            "workspace_bytes": info["workspace_bytes"], "incidences": info["ninc"], "per_batch": {}}
+    for B in synth.WHOLE_BRAIN_BATCHES:
+        draws = synth.coil_minibatches(w.C, B, nsteps + args.warmup, seed=synth.SEED_COILS_DRAW + 100 + B)
+        coil_dev = torch.from_numpy(np.stack(draws)).to(dev)
+        g = sdp_graph.DipStepGraph(A, y_meas, x_hat, B)
+        for i in range(args.warmup):
+            g.step(coil_dev[i])
+        graph_ms = _events_ms(torch, lambda i: g.step(coil_dev[args.warmup + i]), nsteps, flush)
+        n0 = op.launch_count()
+        xg = x_hat.clone().requires_grad_(True)
+
+        def eager(i):
+            xg.grad = None
+            op.dc_loss(A, xg, coil_dev[args.warmup + i], y_meas).backward()
+
+        A.profile(True)
+        A.profile_read()
+        eager_ms = _events_ms(torch, eager, nsteps, flush)
+        prof = A.profile_read()
+        A.profile(False)
+        eager_launches = (op.launch_count() - n0) / nsteps
+        # accuracy gate against the plain form, then the plain form's time
+        ci = coil_dev[0].contiguous()
+        loss_b = g.step(ci)[0].clone()
+        g_b = g.grad.clone()
+        y_b = A.forward(x_hat, ci)
+        y_p, loss_p, g_p = _plain_step(A, torch, x_hat, y_meas, ci, w.K)
+        torch.cuda.synchronize()
+        rel = max(float(torch.linalg.norm(y_p - y_b) / torch.linalg.norm(y_b)),
+                  float(torch.linalg.norm(g_p - g_b) / torch.linalg.norm(g_b)),
+                  abs(float(loss_p) - float(loss_b)) / abs(float(loss_b)))
+        plain_ms = _events_ms(torch, lambda i: _plain_step(A, torch, x_hat, y_meas, coil_dev[i], w.K), 3, flush)
+        model = path_model_bytes(w, B, M)
+        stages = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+        sb = stage_bytes(w, B, M, info["ninc"])
+        per_kernel = {k: {"ms": stages[k], "alg_bytes": sb[k], "frac_of_hbm": sb[k] / (stages[k] * 1e-3) / (hbm * 1e9)}
+                      for k in stages if k in sb}
+        rows["per_batch"][str(B)] = {
+            "dip_step_ms": {"cuda_graph": graph_ms, "eager": eager_ms},
+            "nu_samples_per_s": B * w.J / (graph_ms * 1e-3),
+            "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (graph_ms * 1e-3)},
+            "plain_form": {"ms_per_step": plain_ms, "rel_err_vs_plain": rel, "speedup_vs_graph": plain_ms / graph_ms},
+            "launches_per_step": {"graph": g.launches_per_step, "eager": eager_launches},
+            "kernels": per_kernel}
+        del g, xg, coil_dev
+        if rel > 1e-4:
+            raise SystemExit(f"whole-brain B={B}: batched path differs from the plain form: {rel:.3e}")
+    assert A.status() == 0
+    # the work list: four items with their own TSMI and coil minibatches of 1, 2, 4 and 8
+    xs = [torch.from_numpy(synth.ellipsoid_phantom(w.n, w.K, seed=20 + i)).to(dev)
+          for i in range(len(synth.WHOLE_BRAIN_BATCHES))]
+    cis = [torch.from_numpy(d[0]).to(dev) for d in
+           (synth.coil_minibatches(w.C, B, 1, seed=synth.SEED_COILS_DRAW + 200 + B) for B in synth.WHOLE_BRAIN_BATCHES)]
+    ys = [torch.empty((ci.numel(), w.J), dtype=torch.complex64, device=dev) for ci in cis]
+    outs = [torch.empty_like(x) for x in xs]
+
+    def worklist(i):
+        op.forward_batched([(A, x, ci, y) for x, ci, y in zip(xs, cis, ys)])
+        op.adjoint_batched([(A, y, ci, o, False) for y, ci, o in zip(ys, cis, outs)])
+
+    worklist(0)
+    n0 = op.launch_count()
+    wl_ms = _events_ms(torch, worklist, min(nsteps, 10), flush)
+    wl_launches = (op.launch_count() - n0) / min(nsteps, 10)
+    nsamp = sum(ci.numel() for ci in cis) * w.J
+    model = sum(path_model_bytes(w, ci.numel(), M) for ci in cis)
+    rows["work_list"] = {"batches": list(synth.WHOLE_BRAIN_BATCHES), "fwd_adj_ms": wl_ms,
+                         "nu_samples_per_s": nsamp / (wl_ms * 1e-3), "launches": wl_launches,
+                         "path_model": {"bytes": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (wl_ms * 1e-3)}}
+    assert A.status() == 0
+    A.close()
+    del A, y_meas, x_hat, xs, ys, outs
+    torch.cuda.empty_cache()
+    return rows
+
+
+def multi_volume_rows(args, torch, op, dev, tuning, flush, hbm):
+    """Six independent reconstructions of different matrix sizes (64^3 .. 200x200x160, C in {8,16,32}):
+    one DIP step of every volume (coil minibatch C/4 each) as one batched forward, a residual/loss per
+    volume and one batched adjoint, captured in a CUDA graph; then the full-coil variant (B = C for
+    every volume) against the 150 GB device-memory bound."""
+    vols = synth.MULTI_VOLUME
+    free0, total = torch.cuda.mem_get_info(dev)
+    plans, rows, items = [], [], []
+    t0 = time.perf_counter()
+    for i, w in enumerate(vols):
+        x_true, S, V, omega, frame = synth.make_problem(w)
+        A, plan_s = _upload_plan(op, torch, w, omega, frame, V, S, w.C, dev, tuning)
+        del S
+        y_meas = _measured_kspace(A, torch, x_true, w.C, dev, w.C)
+        x_hat = torch.from_numpy(synth.ellipsoid_phantom(w.n, w.K, seed=1)).to(dev).requires_grad_(False)
+        draws = synth.coil_minibatches(w.C, w.batch, args.warmup + args.steps, seed=synth.SEED_COILS_DRAW + 300 + i)
+        coil_dev = torch.from_numpy(np.stack(draws)).to(dev)
+        info = A.info()
+        M = (info["M1"], info["M2"], info["M3"])
+        plans.append(A)
+        items.append(dict(w=w, A=A, y_meas=y_meas, x=x_hat, draws=coil_dev, M=M,
+                          ci=torch.empty((w.batch,), dtype=torch.int32, device=dev),
+                          yhat=torch.empty((w.batch, w.J), dtype=torch.complex64, device=dev),
+                          grad=torch.empty_like(x_hat), loss=torch.empty((), dtype=torch.float32, device=dev)))
+        rows.append({"volume": w.name, "image": list(w.n), "grid": list(M), "C": w.C, "B": w.batch, "T": w.T,
+                     "J": w.J, "plan_create_s": plan_s, "plan_device_bytes": info["total_bytes"]})
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+
+    def dip_step_all():
+        op.forward_batched([(it["A"], it["x"], it["ci"], it["yhat"]) for it in items])
+        for it in items:
+            it["A"].residual_loss(it["yhat"], it["y_meas"], it["ci"], r2=it["yhat"], loss=it["loss"])
+        op.adjoint_batched([(it["A"], it["yhat"], it["ci"], it["grad"], False) for it in items])
+
+    def set_draw(i):
+        for it in items:
+            it["ci"].copy_(it["draws"][i], non_blocking=True)
+
+    set_draw(0)
+    dip_step_all()
+    torch.cuda.synchronize()
+    # eager, then captured once and replayed
+    n0 = op.launch_count()
+    eager_ms = _events_ms(torch, lambda i: (set_draw(args.warmup + i), dip_step_all()), min(args.steps, 10), flush)
+    eager_launches = (op.launch_count() - n0) / min(args.steps, 10)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            dip_step_all()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    n0 = op.launch_count()
+    with torch.cuda.graph(gr):
+        dip_step_all()
+    graph_launches = op.launch_count() - n0
+    for i in range(args.warmup):
+        set_draw(i)
+        gr.replay()
+    graph_ms = _events_ms(torch, lambda i: (set_draw(args.warmup + i), gr.replay()), args.steps, flush)
+    for p_ in plans:
+        assert p_.status() == 0
+    nsamp = sum(it["w"].batch * it["w"].J for it in items)
+    model = sum(path_model_bytes(it["w"], it["w"].batch, it["M"]) for it in items)
+    out = {"volumes": rows, "setup_s": setup_s,
+           "dip_step_all_volumes_ms": {"cuda_graph": graph_ms, "eager": eager_ms},
+           "nu_samples_per_s": nsamp / (graph_ms * 1e-3),
+           "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (graph_ms * 1e-3)},
+           "launches_per_step": {"graph": graph_launches, "eager": eager_launches}}
+    del gr
+    # full-coil variant: every coil of every volume in one batched forward + adjoint
+    full = [dict(it, ci=torch.arange(it["w"].C, dtype=torch.int32, device=dev),
+                 yhat=torch.empty((it["w"].C, it["w"].J), dtype=torch.complex64, device=dev)) for it in items]
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info(dev)
+
+    def full_step(i):
+        op.forward_batched([(it["A"], it["x"], it["ci"], it["yhat"]) for it in full])
+        op.adjoint_batched([(it["A"], it["yhat"], it["ci"], it["grad"], False) for it in full])
+
+    full_step(0)
+    full_ms = _events_ms(torch, full_step, 3, flush)
+    nfull = sum(it["w"].C * it["w"].J for it in full)
+    fmodel = sum(path_model_bytes(it["w"], it["w"].C, it["M"]) for it in full)
+    out["full_coil"] = {"fwd_adj_ms": full_ms, "nu_samples_per_s": nfull / (full_ms * 1e-3),
+                        "path_model": {"bytes": fmodel, "frac_of_hbm_bound": (fmodel / (hbm * 1e9)) / (full_ms * 1e-3)},
+                        "device_used_gb": (total - free2) / 1e9, "bound_gb": 150.0,
+                        "within_bound": (total - free2) / 1e9 < 150.0}
+    out["device_used_gb"] = {"before": (total - free0) / 1e9, "after_plans": (total - free1) / 1e9,
+                             "full_coil_peak": (total - free2) / 1e9}
+    for p_ in plans:
+        assert p_.status() == 0
+        p_.close()
+    del plans, items, full
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -495,6 +825,14 @@ def run_native(args):
     h2d = xh.numel() * 8 + yh.numel() * 8 + ch.numel() * 4
     d2h = gh.numel() * 8 + 4
 
+    hbm, peak_kind = peaks()
+
+    # ---- whole-brain minibatches and the six-volume batch ----
+    scale = {}
+    if not args.no_scale_rows:
+        scale["whole_brain"] = whole_brain_rows(args, torch, op, dev, tuning, flush, hbm)
+        scale["multi_volume"] = multi_volume_rows(args, torch, op, dev, tuning, flush, hbm)
+
     # ---- rows built on the operator: DCF estimation, SVD-MRF initialiser, CG iteration ----
     from paper_2408_02367_gb300 import recon
 
@@ -608,7 +946,6 @@ def run_native(args):
                     "median of 5, L2 flushed before each, fp16 tensor flops counted with padding to K=16"}
 
     # ---- roofline of the dominant kernel ----
-    hbm, peak_kind = peaks()
     sb = stage_bytes(w, B, M, info["ninc"])
     stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     dom = max(stages, key=lambda k: stages[k]["ms_total"])
@@ -620,7 +957,7 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, B, budget_s=args.cpu_budget)
+        cpu = cpu_baseline(w, B, whole_brain=args.cpu_whole_brain)
 
     if ws > 1:
         dist.barrier()
@@ -653,6 +990,7 @@ def run_native(args):
         "stage_share": step_share,
         "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},
         "operator_rows": rows,
+        "scale_rows": scale,
         "tuning": {"chosen": dict(A.tuning, spread_bins=list(A.tuning["spread_bins"])),
                    "autotuner": tune_table, "note": "forward + adjoint of one coil minibatch per candidate, "
                    "median of 7 with L2 flushed; every candidate checked against the first to 1e-5"},
@@ -677,7 +1015,10 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default kernel shapes instead of the autotuner's")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-whole-brain", action="store_true",
+                    help="also time one coil x all K of the 200x200x160 workload on the CPU oracle")
+    ap.add_argument("--no-scale-rows", action="store_true",
+                    help="skip the whole-brain minibatch rows and the six-volume batch")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed DIP steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)

@@ -77,6 +77,21 @@ void sdp_dm_destroy(sdp_dm_t dm);
  */
 int sdp_dm_match(sdp_dm_t dm, const void* x, int64_t nvox, int32_t* idx, void* pd, float* qmap, void* stream);
 
+/*
+ * Test hook for the bounded waits of the GEMM kernel (the paper has no
+ * counterpart).  Every later sdp_dm_match of this matcher uses `timeout_ns`
+ * as the limit of each mbarrier wait (0: the default of one second; else
+ * 1e3 .. 1e10 ns), and, when withhold_tile >= 0, the first CTA's producer
+ * never copies atom tile `withhold_tile` of its first voxel-tile pair: the
+ * MMA threads' wait for that tile runs out, the kernel records SDP_ERR_TIMEOUT,
+ * its CTA stops, waits (bounded) for the copies and MMAs it issued and frees
+ * its tensor memory, and the match's outputs are not valid (they stay in
+ * range).  withhold_tile = -1 turns the hook off.  Nothing faults or hangs:
+ * this exercises the timeout path on the device.  SDP_ERR_INVALID_ARG for
+ * withhold_tile outside [-1, atom tiles) or a limit out of range.
+ */
+int sdp_dm_set_wait_test(sdp_dm_t dm, int32_t withhold_tile, int64_t timeout_ns);
+
 /* Synchronise `stream`, return the matcher's device status word and clear it. */
 int sdp_dm_status(sdp_dm_t dm, void* stream);
 

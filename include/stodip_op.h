@@ -53,8 +53,20 @@ extern "C" {
 #define SDP_ERR_BOUNDS 5        /* device-side index check failed (coil index) */
 #define SDP_ERR_UNSUPPORTED 6   /* parameters outside the supported range */
 
-/* Plan flags (bit mask). */
+/*
+ * Plan flags (bit mask).
+ *   SDP_FLAG_BORROW_MAPS  the plan keeps the caller's coil_maps pointer instead
+ *                         of copying the maps (C x N1 N2 N3 x 8 bytes: 1.6 GB for
+ *                         32 coils at 200 x 200 x 160).  The caller keeps that
+ *                         DEVICE buffer alive and unchanged until
+ *                         sdp_plan_destroy; kernels only read it.
+ * Other bits are reserved: a plan whose flags hold one gets SDP_ERR_INVALID_ARG.
+ * (The spread is always deterministic, bitwise: every grid point is written
+ * exactly once; and the adjoint never needs the forward's grid, so the plan has
+ * nothing to recompute.  Neither needs a flag.)
+ */
 #define SDP_FLAG_NONE 0u
+#define SDP_FLAG_BORROW_MAPS 1u
 
 /* Opaque plan, owned by the library. */
 typedef struct sdp_plan_s* sdp_plan_t;
@@ -79,7 +91,9 @@ typedef struct sdp_plan_s* sdp_plan_t;
  *   traj           DEVICE float32 [J][3], omega in radians, |omega_d| <= pi;
  *                  omega[:, d] pairs with image axis d.  Read during create only.
  *   V              DEVICE complex64 [T][K] temporal subspace basis, copied.
- *   coil_maps      DEVICE complex64 [C][N1][N2][N3] coil sensitivities S_c, copied.
+ *   coil_maps      DEVICE complex64 [C][N1][N2][N3] coil sensitivities S_c, copied
+ *                  (or borrowed, with SDP_FLAG_BORROW_MAPS).
+ *   flags          SDP_FLAG_NONE or SDP_FLAG_BORROW_MAPS.
  */
 typedef struct {
     int64_t n[3];
@@ -211,8 +225,10 @@ int sdp_adjoint_scaled(sdp_plan_t plan, const void* y, const int32_t* coil_idx, 
  *   y_meas    DEVICE complex64 [n_meas_rows][J] (e.g. all C coils, or one row per b)
  *   meas_idx  DEVICE int32 [B], rows of y_meas, each in [0, n_meas_rows)
  *   r2        DEVICE complex64 [B][J] (overwritten)
- *   loss      DEVICE float32 scalar (overwritten); accumulated in float64 and
- *             summed in a fixed order, so it is bitwise repeatable.
+ *   loss      DEVICE float32 scalar (overwritten).  Each thread adds the
+ *             |r|^2 of its 4 entries and each warp its 128 entries in float32;
+ *             the warps of a block and then the blocks are added in float64,
+ *             every sum in a fixed order, so the loss is bitwise repeatable.
  */
 int sdp_residual_loss(sdp_plan_t plan, const void* yhat, const void* y_meas, int32_t n_meas_rows,
                       const int32_t* meas_idx, int32_t B, void* r2, float* loss, void* stream);
@@ -298,10 +314,14 @@ int sdp_adjoint_batched(const sdp_work* items, int32_t n, void* stream);
  * allocator must account for every byte, a process under a hard memory cap,
  * or work recorded while allocation is forbidden), who therefore cannot
  * create a plan.
+ *   It computes what sdp_residual_loss computes, i.e. sdp_residual_loss_weighted
+ *   with dcf = NULL: there is no density compensation (every sample weight 1).
  *   yhat, y_meas, meas_idx, r2, loss: as in sdp_residual_loss (DEVICE);
  *   B >= 1 rows of yhat, J >= 1 samples per row, B * J <= SDP_NOALLOC_MAX_ELEMS,
  *   larger sizes return SDP_ERR_INVALID_ARG.  Rows of meas_idx outside
- *   [0, n_meas_rows) contribute a zero residual (there is no status word).
+ *   [0, n_meas_rows) contribute a zero residual and raise no SDP_ERR_BOUNDS
+ *   (there is no status word).  |r|^2 is added in float32 four entries at a
+ *   time per thread and in float64 from there on, in a fixed order.
  * Scratch: a fixed 32 KB + 256 B array inside the library image on every
  * device that loads the library, held until the process exits.  The first
  * call on a device looks its address up (cudaGetSymbolAddress, with that
@@ -336,6 +356,14 @@ double sdp_plan_beta(sdp_plan_t plan);
 
 /* Bytes of device workspace the plan holds for its max_batch (0 for NULL). */
 size_t sdp_workspace_bytes(sdp_plan_t plan);
+
+/*
+ * Bytes of device workspace a plan of the same geometry, trajectory and kernel
+ * shapes would hold for a coil minibatch of up to maxB coils (1..64), for
+ * callers that size several plans against a memory budget; 0 for a NULL plan or
+ * maxB out of range.  Host only, no device work.
+ */
+size_t sdp_workspace_bytes_for(sdp_plan_t plan, int32_t maxB);
 
 /* Kernels launched by this library in this process so far (all plans). */
 int64_t sdp_launch_count(void);

@@ -380,7 +380,10 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     SDP_TRY(dev_alloc(p, &p->tframe, (size_t)J));
     SDP_TRY(dev_alloc(p, &p->wts, (size_t)J * 3 * W));
     SDP_TRY(dev_alloc(p, &p->V, (size_t)d->T * Kz));
-    SDP_TRY(dev_alloc(p, &p->S, (size_t)d->C * nvox));
+    if (d->flags & SDP_FLAG_BORROW_MAPS)
+        p->S = const_cast<float2*>(static_cast<const float2*>(d->coil_maps));   // read only, caller-owned
+    else
+        SDP_TRY(dev_alloc(p, &p->S, (size_t)d->C * nvox));
     SDP_TRY(dev_alloc(p, &p->dinv, dinv.size()));
     SDP_TRY(dev_alloc(p, &p->tw, tw.size()));
     SDP_TRY(dev_alloc(p, &p->inc, inc.size()));
@@ -403,7 +406,9 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     SDP_CUDA(cudaMemcpyAsync(p->pts, pts.data(), pts.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->tframe, tf.data(), tf.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->V, d->V, (size_t)d->T * Kz * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    SDP_CUDA(cudaMemcpyAsync(p->S, d->coil_maps, (size_t)d->C * nvox * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (!(d->flags & SDP_FLAG_BORROW_MAPS))
+        SDP_CUDA(cudaMemcpyAsync(p->S, d->coil_maps, (size_t)d->C * nvox * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                 st));
     SDP_CUDA(cudaMemcpyAsync(p->dinv, dinv.data(), dinv.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->inc, inc.data(), inc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -638,6 +643,9 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
     if (d->K < 1 || d->K > kMaxK) return SDP_ERR_UNSUPPORTED;
     if (d->T < 1 || d->C < 1 || d->J < 1 || d->J >= (1LL << 31)) return SDP_ERR_INVALID_ARG;
     if (d->max_batch < 1 || d->max_batch > kMaxBatch) return SDP_ERR_INVALID_ARG;
+    if (d->flags & ~(uint32_t)SDP_FLAG_BORROW_MAPS) return SDP_ERR_INVALID_ARG;
+    if ((d->flags & SDP_FLAG_BORROW_MAPS) && (reinterpret_cast<uintptr_t>(d->coil_maps) % alignof(float2)))
+        return SDP_ERR_INVALID_ARG;
     if (d->frame_offsets[0] != 0 || d->frame_offsets[d->T] != d->J) return SDP_ERR_INVALID_ARG;
     for (int t = 0; t < d->T; ++t)
         if (d->frame_offsets[t + 1] < d->frame_offsets[t]) return SDP_ERR_INVALID_ARG;
@@ -782,6 +790,14 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
 double sdp_plan_beta(sdp_plan_t p) { return p ? p->beta : -1.0; }
 
 size_t sdp_workspace_bytes(sdp_plan_t p) { return p ? p->workspace_bytes : 0; }
+
+size_t sdp_workspace_bytes_for(sdp_plan_t p, int32_t maxB) {
+    if (!p || maxB < 1 || maxB > kMaxBatch) return 0;
+    const long long G = p->M[0] * p->M[1] * p->M[2];
+    const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);
+    const size_t gridB = (size_t)(p->n[0] * p->M[1] * p->M[2]);
+    return (gridA + gridB) * (size_t)p->geo.K * (size_t)maxB * sizeof(float2);
+}
 
 int64_t sdp_launch_count(void) { return g_launches.load(); }
 

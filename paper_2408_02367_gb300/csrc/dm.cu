@@ -48,7 +48,7 @@ constexpr int NB = 8;                       // atom-tile ring stages
 constexpr int kEpiWarps = 16;               // 2 voxel tiles x 2 column halves x 4 lane quarters
 constexpr int kThreadsG = 128 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;         // 2 buffers x 2 voxel tiles x 128 columns
-constexpr unsigned long long kTimeoutNs = 1000000000ull;
+constexpr unsigned long long kTimeoutNs = 1000000000ull;   // default limit of every mbarrier wait
 constexpr int kMinSmem = 120 * 1024;        // keeps one CTA (and one tensor-memory owner) per SM
 
 // ---------------------------------------------------------------------------
@@ -141,15 +141,16 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Bounded wait for the completion of the phase of `bar` with parity `parity`.
-// Gives up after kTimeoutNs (recording SDP_ERR_TIMEOUT and raising the
-// block's abort flag), or at once when the abort flag is up and `honour_abort`.
+// Gives up after `limit_ns` of %globaltimer (recording SDP_ERR_TIMEOUT and
+// raising the block's abort flag), or at once when the abort flag is up and
+// `honour_abort`.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                          bool honour_abort) {
+                                          bool honour_abort, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
         if (honour_abort && *abort_flag) return false;
-        if (gtimer() - t0 > kTimeoutNs) {
+        if (gtimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicCAS(status, 0, SDP_ERR_TIMEOUT);
             return false;
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) dm_refine(const float2* __restrict__ x, l
                                                  const float* __restrict__ best_score,
                                                  const int* __restrict__ best_chunk,
                                                  const float2* __restrict__ dhat, const float* __restrict__ inv_norm,
-                                                 long long P, const float2* __restrict__ params,
+                                                 long long P, int nchunk, const float2* __restrict__ params,
                                                  int* __restrict__ idx, float2* __restrict__ pd,
                                                  float2* __restrict__ qmap) {
     const int lane = threadIdx.x & 31;
@@ -258,6 +259,8 @@ __global__ void __launch_bounds__(256) dm_refine(const float2* __restrict__ x, l
         const float s0 = __ldg(best_score + v), s1 = __ldg(best_score + nvox + v);
         const int c0 = __ldg(best_chunk + v), c1 = __ldg(best_chunk + nvox + v);
         cl = (s1 > s0 || (s1 == s0 && c1 < c0)) ? c1 : c0;
+        // after a timed-out score kernel the chunk may be stale: keep every load in range
+        cl = min(max(cl, 0), nchunk - 1);
     }
     long long p[RV];
     float2 s[RV];
@@ -318,6 +321,8 @@ struct GemmArgs {
     float* best_score;      // [2][nvox]: per column half, the best fp16-path score
     int* best_chunk;        // [2][nvox]: and its chunk
     int* status;
+    unsigned long long timeout_ns;   // limit of every mbarrier wait
+    int withhold_tile;      // test hook: CTA 0 never copies this atom tile of its first step (-1: off)
 };
 
 // Largest |d^H x|^2 over the 16 atoms of 32 accumulator columns laid out
@@ -412,14 +417,20 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             for (int i = 0; i < nsteps && ok; ++i) {
                 const int pair = (int)blockIdx.x + i * (int)gridDim.x;
                 const int sa = i & 1;
-                if (!mbar_wait(smem_u32(a_empty + sa), ((i >> 1) & 1) ^ 1, abort_flag, g.status, true)) break;
+                if (!mbar_wait(smem_u32(a_empty + sa), ((i >> 1) & 1) ^ 1, abort_flag, g.status, true, g.timeout_ns)) break;
                 mbar_expect_tx(smem_u32(a_full + sa), VT * TB);
                 bulk_g2s(smem_u32(sA + sa * VT * TB), g.xh + (size_t)pair * VT * TB, VT * TB, smem_u32(a_full + sa));
                 ++na;
                 for (int t = 0; t < ntiles; ++t) {
+                    if (i == 0 && t == g.withhold_tile && blockIdx.x == 0) {
+                        // test hook: this copy is never issued, so the MMA threads' bounded
+                        // wait for it runs out; stop producing and drain what was issued
+                        ok = false;
+                        break;
+                    }
                     const int s = (int)(nb % NB);
                     if (!mbar_wait(smem_u32(b_empty + s), (uint32_t)((nb / NB) & 1) ^ 1u, abort_flag, g.status,
-                                   true)) {
+                                   true, g.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -430,10 +441,10 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             }
             // drain: the last copy into every slot has landed before the block may exit
             for (int s = 0; s < 2; ++s)
-                if (na > s) mbar_wait(smem_u32(a_full + s), (uint32_t)(((na - 1 - s) / 2) & 1), abort_flag, g.status, false);
+                if (na > s) mbar_wait(smem_u32(a_full + s), (uint32_t)(((na - 1 - s) / 2) & 1), abort_flag, g.status, false, g.timeout_ns);
             for (int s = 0; s < NB; ++s)
                 if (nb > s)
-                    mbar_wait(smem_u32(b_full + s), (uint32_t)(((nb - 1 - s) / NB) & 1), abort_flag, g.status, false);
+                    mbar_wait(smem_u32(b_full + s), (uint32_t)(((nb - 1 - s) / NB) & 1), abort_flag, g.status, false, g.timeout_ns);
         }
     } else if (warp == 1 || warp == 3) {
         if (lane == 0) {
@@ -447,14 +458,14 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             bool ok = true;
             for (int i = 0; i < nsteps && ok; ++i) {
                 const int sa = i & 1;
-                if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((i >> 1) & 1), abort_flag, g.status, true)) break;
+                if (!mbar_wait(smem_u32(a_full + sa), (uint32_t)((i >> 1) & 1), abort_flag, g.status, true, g.timeout_ns)) break;
                 tc_fence_after();
                 for (int t = 0; t < ntiles; ++t, ++nb) {
                     const int s = (int)(nb % NB);
                     const int b = (int)(nb % NACC);
-                    if (!mbar_wait(smem_u32(b_full + s), (uint32_t)((nb / NB) & 1), abort_flag, g.status, true) ||
+                    if (!mbar_wait(smem_u32(b_full + s), (uint32_t)((nb / NB) & 1), abort_flag, g.status, true, g.timeout_ns) ||
                         !mbar_wait(smem_u32(acce + b), (uint32_t)((nb / NACC) & 1) ^ 1u, abort_flag, g.status,
-                                   true)) {
+                                   true, g.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -473,7 +484,7 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             }
             // every MMA this thread issued has completed before the tensor memory is freed
             tc_commit(smem_u32(mma_done + u));
-            mbar_wait(smem_u32(mma_done + u), 0, abort_flag, g.status, false);
+            mbar_wait(smem_u32(mma_done + u), 0, abort_flag, g.status, false, g.timeout_ns);
         }
     } else if (warp >= 4) {
         const int eg = warp - 4;
@@ -490,7 +501,7 @@ __global__ void __launch_bounds__(kThreadsG, 1) dm_score_kernel(GemmArgs g) {
             for (int t = 0; t < ntiles; ++t, ++nb) {
                 const int b = (int)(nb % NACC);
                 const bool w = mbar_wait(smem_u32(acc_full + u * NACC + b), (uint32_t)((nb / NACC) & 1), abort_flag, g.status,
-                                         true);
+                                         true, g.timeout_ns);
                 if (!__all_sync(0xffffffffu, w)) {     // warp-uniform: tcgen05.ld is .sync.aligned
                     ok = false;
                     break;
@@ -550,6 +561,8 @@ struct sdp_dm_s {
     int* best = nullptr;
     int* status = nullptr;
     size_t bytes = 0;
+    unsigned long long timeout_ns = sdp::kTimeoutNs;
+    int withhold_tile = -1;
 };
 
 namespace {
@@ -631,6 +644,8 @@ int sdp_dm_create(sdp_dm_t* out, const void* atoms, const float* params, int64_t
     const int smem_req = std::max(smem, sdp::kMinSmem);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(d->status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->best, 0, (size_t)2 * max_vox * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->best_score, 0, (size_t)2 * max_vox * sizeof(float), st);
     if (e == cudaSuccess)
         e = d->KS == 1 ? cudaFuncSetAttribute(sdp::dm_score_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_req)
@@ -658,7 +673,8 @@ int sdp_dm_match(sdp_dm_t dm, const void* x, int64_t nvox, int32_t* idx, void* p
     const long long nrows = npairs * sdp::VT * sdp::BM;
     const float2* xv = static_cast<const float2*>(x);
     sdp::dm_prep_voxels<<<(unsigned)((nrows + 255) / 256), 256, 0, st>>>(xv, nvox, dm->K, dm->KS, nrows, dm->xh);
-    GemmArgs a{dm->xh, dm->bh, nvox, (int)npairs, dm->ntiles, dm->best_score, dm->best, dm->status};
+    GemmArgs a{dm->xh, dm->bh, nvox, (int)npairs, dm->ntiles, dm->best_score, dm->best, dm->status,
+               dm->timeout_ns, dm->withhold_tile};
     const unsigned grid = (unsigned)std::min<long long>(npairs, dm->nsm);
     const int smem = std::max(dm->KS == 1 ? sdp::score_smem_bytes<1>() : sdp::score_smem_bytes<2>(), sdp::kMinSmem);
     if (dm->KS == 1)
@@ -667,10 +683,19 @@ int sdp_dm_match(sdp_dm_t dm, const void* x, int64_t nvox, int32_t* idx, void* p
         sdp::dm_score_kernel<2><<<grid, sdp::kThreadsG, smem, st>>>(a);
     sdp::dm_refine<<<(unsigned)((nvox + 8 * sdp::RV - 1) / (8 * sdp::RV)), 256, 0, st>>>(xv, nvox, dm->K, dm->best_score, dm->best, dm->dhat,
                                                                dm->inv_norm,
-                                                               dm->P, dm->params, idx, static_cast<float2*>(pd),
+                                                               dm->P, 2 * dm->ntiles, dm->params, idx,
+                                                               static_cast<float2*>(pd),
                                                                reinterpret_cast<float2*>(qmap));
     sdp::note_launches(3);
     if (cudaGetLastError() != cudaSuccess) return SDP_ERR_CUDA;
+    return SDP_OK;
+}
+
+int sdp_dm_set_wait_test(sdp_dm_t dm, int32_t withhold_tile, int64_t timeout_ns) {
+    if (!dm || withhold_tile < -1 || withhold_tile >= dm->ntiles) return SDP_ERR_INVALID_ARG;
+    if (timeout_ns != 0 && (timeout_ns < 1000 || timeout_ns > 10000000000LL)) return SDP_ERR_INVALID_ARG;
+    dm->withhold_tile = withhold_tile;
+    dm->timeout_ns = timeout_ns == 0 ? sdp::kTimeoutNs : (unsigned long long)timeout_ns;
     return SDP_OK;
 }
 

@@ -27,6 +27,10 @@ constexpr long long kChunk = 1LL << 16;
 constexpr int kMaxChunks = 4096;           // 4096 chunks x 2^16 = 2^28 entries
 constexpr int kMaxDevices = 64;
 
+// The fixed scratch must hold one partial per chunk of the largest accepted call.
+static_assert((long long)kMaxChunks * kChunk >= SDP_NOALLOC_MAX_ELEMS,
+              "noalloc scratch holds fewer chunk partials than SDP_NOALLOC_MAX_ELEMS needs");
+
 struct NoAllocScratch {
     double partials[kMaxChunks];
     unsigned int counter;
@@ -40,7 +44,12 @@ NoAllocScratch* g_ptr[kMaxDevices] = {};
 
 // One block per chunk of the flattened [B][J] residual; each block reduces its
 // chunk in a fixed order, the last block to finish sums the chunk partials in
-// chunk order.
+// chunk order.  A thread takes the entries e0 + tid + 256 i of its chunk and
+// adds their |r|^2 in float32 four at a time, then the group sum into a float64
+// accumulator (the FP64 pipe of this part is far too narrow for per-entry
+// float64 work).  Its row b and offset j are found once with one division and
+// then advanced by the stride; the division runs again only when j passes the
+// end of a row.
 __global__ void __launch_bounds__(kThreads) residual_loss_chunked_kernel(
     const float2* yhat, const float2* __restrict__ ymeas, const int* __restrict__ meas_idx, long long J,
     int nrows, long long total, float2* r2, NoAllocScratch* scr, float* __restrict__ loss) {
@@ -48,10 +57,13 @@ __global__ void __launch_bounds__(kThreads) residual_loss_chunked_kernel(
     __shared__ bool s_last;
     const long long e0 = (long long)blockIdx.x * kChunk;
     const long long e1 = e0 + kChunk < total ? e0 + kChunk : total;
+    long long e = e0 + threadIdx.x;
+    long long b = e / J;
+    long long j = e - b * J;
     double acc = 0.0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += kThreads) {
-        const int b = (int)(e / J);
-        const long long j = e - (long long)b * J;
+    float part = 0.f;
+    int nin = 0;
+    for (; e < e1; e += kThreads) {
         const int row = __ldg(meas_idx + b);
         float2 r = make_float2(0.f, 0.f);
         if (row >= 0 && row < nrows) {
@@ -59,9 +71,20 @@ __global__ void __launch_bounds__(kThreads) residual_loss_chunked_kernel(
             const float2 m = __ldg(ymeas + (long long)row * J + j);
             r = make_float2(h.x - m.x, h.y - m.y);
         }
-        acc += (double)r.x * r.x + (double)r.y * r.y;
+        part = fmaf(r.x, r.x, fmaf(r.y, r.y, part));
+        if (++nin == 4) {
+            acc += (double)part;
+            part = 0.f;
+            nin = 0;
+        }
         r2[e] = make_float2(2.f * r.x, 2.f * r.y);
+        j += kThreads;
+        if (j >= J) {
+            b += j / J;
+            j %= J;
+        }
     }
+    acc += (double)part;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();

@@ -67,6 +67,12 @@ class DictionaryMatcher:
                "sdp_dm_match")
         return (idx, pd, qm) if qmap else (idx, pd)
 
+    def set_wait_test(self, withhold_tile: int = -1, timeout_ns: int = 0):
+        """Test hook of the GEMM kernel's bounded waits (sdp_dm_set_wait_test): later matches use
+        `timeout_ns` per wait (0: one second) and, for withhold_tile >= 0, the first CTA never copies that
+        atom tile, so its wait runs out and the match reports SDP_ERR_TIMEOUT through status()."""
+        _check(lib().sdp_dm_set_wait_test(self._h, int(withhold_tile), int(timeout_ns)), "sdp_dm_set_wait_test")
+
     def status(self) -> int:
         return int(lib().sdp_dm_status(self._h, _stream_ptr(self.device)))
 

@@ -134,6 +134,7 @@ EXPORTS = {
     "sdp_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "sdp_plan_beta": (ctypes.c_double, [ctypes.c_void_p]),
     "sdp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "sdp_workspace_bytes_for": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32]),
     "sdp_launch_count": (ctypes.c_int64, []),
     "sdp_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "sdp_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -148,6 +149,7 @@ EXPORTS = {
     "sdp_dm_match": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sdp_dm_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sdp_dm_set_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "sdp_dm_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
 }
 
@@ -208,7 +210,8 @@ class SubspaceNufft:
     V         complex64 [T][K] (device), coil_maps complex64 [C][N1][N2][N3] (device).
     """
 
-    def __init__(self, traj, frame_offsets, n, width, oversamp, V, coil_maps, max_batch=1, tuning=None):
+    def __init__(self, traj, frame_offsets, n, width, oversamp, V, coil_maps, max_batch=1, tuning=None,
+                 borrow_maps=False):
         if not torch.cuda.is_available():
             raise RuntimeError("SubspaceNufft needs a CUDA device (no CPU fallback)")
         self.device = traj.device
@@ -232,7 +235,9 @@ class SubspaceNufft:
         d.width = int(width)
         d.K, d.T, d.C, d.J = int(K), int(T), int(C), int(J)
         d.max_batch = int(max_batch)
-        d.flags = 0
+        # SDP_FLAG_BORROW_MAPS: the plan reads the caller's coil_maps; this object keeps the tensor alive
+        d.flags = 1 if borrow_maps else 0
+        self._borrowed_maps = coil_maps if borrow_maps else None
         d.frame_offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         d.traj = traj.data_ptr()
         d.V = V.data_ptr()
@@ -279,6 +284,10 @@ class SubspaceNufft:
     def grid(self):
         i = self.info()
         return (i["M1"], i["M2"], i["M3"])
+
+    def workspace_bytes_for(self, max_batch):
+        """Workspace a plan of this geometry would hold for minibatches of up to max_batch coils."""
+        return int(lib().sdp_workspace_bytes_for(self._h, int(max_batch)))
 
     def launches_per_step(self, B):
         """Kernel launches of one dc_loss forward + backward on B coils (all K channels):
@@ -543,13 +552,14 @@ def tv_loss(op: SubspaceNufft, x, lam: float, eps: float = 1e-6):
     return _TotalVariation.apply(x, op, float(lam), float(eps))
 
 
-def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda", tuning=None):
-    """Plan from numpy inputs (omega float32 [J][3], frame int [J] non-decreasing)."""
+def make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device="cuda", tuning=None, borrow_maps=False):
+    """Plan from numpy inputs (omega float32 [J][3], frame int [J] non-decreasing); S may also be a
+    complex64 device tensor, which the plan then borrows when borrow_maps is set."""
     T = V.shape[0]
     off = np.searchsorted(np.asarray(frame), np.arange(T + 1), side="left").astype(np.int64)
     off[-1] = len(frame)
     dev = torch.device(device)
+    St = S if isinstance(S, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev)
     return SubspaceNufft(torch.from_numpy(np.ascontiguousarray(omega, np.float32)).to(dev), off, n, width,
                          oversamp, torch.from_numpy(np.ascontiguousarray(V, np.complex64)).to(dev),
-                         torch.from_numpy(np.ascontiguousarray(S, np.complex64)).to(dev), max_batch=max_batch,
-                         tuning=tuning)
+                         St, max_batch=max_batch, tuning=tuning, borrow_maps=borrow_maps)

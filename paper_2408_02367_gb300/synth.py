@@ -68,6 +68,21 @@ WORKLOADS = {
     "vol24_w6": Workload("vol24_w6", (24, 24, 24), 5, 4, 100, 1, 512, 6, 2.0, 2),
 }
 
+# Whole-brain coil minibatches: one 200x200x160, C=32 volume applied to a work list
+# of uneven minibatches (each item with its own TSMI).
+WHOLE_BRAIN_BATCHES = (1, 2, 4, 8)
+
+# Six independent reconstructions of different matrix sizes in one batch: 1024-sample
+# arms, one arm per frame, coil minibatch C/4 per volume, W=4, sigma=1.25, K=5.
+MULTI_VOLUME = (
+    Workload("mv64", (64, 64, 64), 5, 8, 300, 1, 1024, 4, 1.25, 2),
+    Workload("mv96", (96, 96, 96), 5, 8, 400, 1, 1024, 4, 1.25, 2),
+    Workload("mv128", (128, 128, 128), 5, 16, 500, 1, 1024, 4, 1.25, 4),
+    Workload("mv128x96", (128, 128, 96), 5, 16, 600, 1, 1024, 4, 1.25, 4),
+    Workload("mv160", (160, 160, 160), 5, 32, 800, 1, 1024, 4, 1.25, 8),
+    Workload("mv200x160", (200, 200, 160), 5, 32, 1000, 1, 1024, 4, 1.25, 8),
+)
+
 
 def golden_means_3d():
     """Multidimensional golden means for 3D direction sampling.
@@ -117,10 +132,19 @@ def spiral_trajectory(T: int, arms: int, arm_len: int, dtype=np.float32):
     return omega, frame
 
 
+def _fftn(a, inverse=False):
+    """3D FFT over the last three axes on every host core (scipy.fft), else numpy."""
+    try:
+        import scipy.fft as sf
+        return (sf.ifftn if inverse else sf.fftn)(a, axes=(-3, -2, -1), workers=-1)
+    except ImportError:
+        return (np.fft.ifftn if inverse else np.fft.fftn)(a, axes=(-3, -2, -1))
+
+
 def _smooth_fft(vol: np.ndarray, sigma_vox: float) -> np.ndarray:
     """Gaussian smoothing (periodic) of the last three axes by FFT multiplication."""
     shp = vol.shape[-3:]
-    f = np.fft.fftn(vol, axes=(-3, -2, -1))
+    f = _fftn(vol)
     g = np.ones(shp)
     for d, nd in enumerate(shp):
         fr = np.fft.fftfreq(nd)
@@ -128,7 +152,7 @@ def _smooth_fft(vol: np.ndarray, sigma_vox: float) -> np.ndarray:
         sh = [1, 1, 1]
         sh[d] = nd
         g = g * gd.reshape(sh)
-    return np.fft.ifftn(f * g, axes=(-3, -2, -1))
+    return _fftn(f * g, inverse=True)
 
 
 def _centred_coords(n):
@@ -144,9 +168,7 @@ def ellipsoid_phantom(n, K: int, seed: int = SEED_PHANTOM, n_ell: int = 12, dtyp
     smoothed with a Gaussian of one voxel.  Returns x [K][N1][N2][N3].
     """
     rng = np.random.default_rng(seed)
-    c1, c2, c3 = _centred_coords(n)
-    X, Y, Z = np.meshgrid(c1, c2, c3, indexing="ij")
-    P = np.stack([X, Y, Z], axis=-1)
+    coords = _centred_coords(n)
     x = np.zeros((K,) + tuple(n), dtype=np.complex128)
     for _ in range(n_ell):
         ctr = rng.uniform(-0.6, 0.6, size=3)
@@ -154,9 +176,18 @@ def ellipsoid_phantom(n, K: int, seed: int = SEED_PHANTOM, n_ell: int = 12, dtyp
         q, _r = np.linalg.qr(rng.standard_normal((3, 3)))
         amp = (rng.standard_normal(K) + 1j * rng.standard_normal(K)) / np.sqrt(2.0)
         amp = amp / (np.arange(K) + 1.0)
-        loc = (P - ctr) @ q
+        # only the voxels within the ellipsoid's bounding sphere (radius max(ax)) can lie inside it
+        sl = []
+        for d, u in enumerate(coords):
+            idx = np.nonzero(np.abs(u - ctr[d]) <= ax.max() + 1e-12)[0]
+            sl.append(slice(idx[0], idx[-1] + 1) if idx.size else slice(0, 0))
+        if any(v.stop <= v.start for v in sl):
+            continue
+        X, Y, Z = np.meshgrid(coords[0][sl[0]], coords[1][sl[1]], coords[2][sl[2]], indexing="ij")
+        loc = (np.stack([X, Y, Z], axis=-1) - ctr) @ q
         inside = np.sum((loc / ax) ** 2, axis=-1) <= 1.0
-        x[:, inside] += amp[:, None]
+        sub = x[:, sl[0], sl[1], sl[2]]
+        sub[:, inside] += amp[:, None]
     x = _smooth_fft(x, 1.0)
     return x.astype(dtype)
 
@@ -168,21 +199,30 @@ def coil_maps(n, C: int, dtype=np.complex64):
     magnitude is a Gaussian with standard deviation 0.6 FOV and its phase is 2*pi*c/C plus a small
     linear ramp.  Returns S [C][N1][N2][N3].
     """
-    c1, c2, c3 = _centred_coords(n)
-    X, Y, Z = np.meshgrid(c1, c2, c3, indexing="ij")
-    S = np.empty((C,) + tuple(n), dtype=np.complex128)
+    # Both the Gaussian magnitude and the linear phase ramp factor over the axes, so
+    # coil c is the outer product of three 1-D complex profiles (times its constant
+    # phase); only the root-sum-of-squares normalisation couples the coils.
+    coords = _centred_coords(n)
     ga = np.pi * (3.0 - math.sqrt(5.0))
+    prof = []
     for c in range(C):
         zc = 1.0 - 2.0 * (c + 0.5) / C
         rc = math.sqrt(max(0.0, 1.0 - zc * zc))
         d = np.array([rc * math.cos(ga * c), rc * math.sin(ga * c), zc]) * 1.2
-        dist2 = (X - d[0]) ** 2 + (Y - d[1]) ** 2 + (Z - d[2]) ** 2
-        mag = np.exp(-dist2 / (2.0 * 1.2 ** 2))  # std 0.6 FOV = 1.2 in FOV/2 units
-        ramp = 0.3 * (d[0] * X + d[1] * Y + d[2] * Z)
-        S[c] = mag * np.exp(1j * (2.0 * np.pi * c / C + ramp))
-    rss = np.sqrt(np.sum(np.abs(S) ** 2, axis=0))
-    S /= rss[None]
-    return S.astype(dtype)
+        # magnitude exp(-|r - d|^2 / (2 * 1.2^2)) (std 0.6 FOV = 1.2 in FOV/2 units), phase ramp 0.3 d.r
+        a = [np.exp(-(u - d[i]) ** 2 / (2.0 * 1.2 ** 2)) * np.exp(1j * 0.3 * d[i] * u)
+             for i, u in enumerate(coords)]
+        a[0] = a[0] * np.exp(1j * 2.0 * np.pi * c / C)
+        prof.append(a)
+    ss = np.zeros(tuple(n))
+    for a in prof:
+        m = [np.abs(v) ** 2 for v in a]
+        ss += m[0][:, None, None] * m[1][None, :, None] * m[2][None, None, :]
+    inv_rss = 1.0 / np.sqrt(ss)
+    S = np.empty((C,) + tuple(n), dtype=dtype)
+    for c, a in enumerate(prof):
+        S[c] = (a[0][:, None, None] * a[1][None, :, None] * a[2][None, None, :]) * inv_rss
+    return S
 
 
 def subspace_basis(T: int, K: int, seed: int = SEED_V, real: bool = False, dtype=np.complex64):

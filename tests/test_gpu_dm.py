@@ -138,3 +138,31 @@ def test_voxel_shapes_tiny_and_empty_calls():
     assert M.status() == 0
     info = M.info()
     assert info["P"] == 70 and info["K"] == 3 and info["ksteps"] == 1 and info["atom_tiles"] == 2
+
+
+def test_bounded_wait_runs_out_reports_timeout_then_recovers():
+    """The GEMM kernel's mbarrier waits are bounded.  With the test hook, the first
+    CTA's producer never copies one atom tile, so the MMA threads' wait for it runs
+    out after a 20 ms limit: the match must report SDP_ERR_TIMEOUT (no fault, no
+    hang), the context must stay usable, and the next match with the hook off must
+    be correct again."""
+    from paper_2408_02367_gb300 import dm
+    P, nvox, K = 1000, 5000, 5                                   # 16 atom tiles
+    D = random_atoms(P, K, 41)
+    x, p, _ = synth.dm_volume(D, nvox, noise=0.0, seed=42)
+    M = dm.DictionaryMatcher(_t(D), max_vox=nvox)
+    with pytest.raises(Exception):
+        M.set_wait_test(withhold_tile=16)                        # past the last atom tile
+    with pytest.raises(Exception):
+        M.set_wait_test(withhold_tile=0, timeout_ns=10)          # limit below 1 us
+    M.set_wait_test(withhold_tile=3, timeout_ns=20_000_000)
+    idx, pd = M.match(_t(x))
+    assert M.status() == 4                                       # SDP_ERR_TIMEOUT
+    assert M.status() == 0                                       # read and cleared
+    ii = idx.cpu().numpy()
+    assert ii.min() >= 0 and ii.max() < P                        # invalid but in range
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0      # the context still works
+    M.set_wait_test(-1, 0)
+    idx, pd = M.match(_t(x))
+    assert M.status() == 0
+    check(D, x, idx.cpu().numpy(), pd.cpu().numpy(), expect_unique_frac=0.9)

@@ -1,16 +1,20 @@
-"""Parity at the full workload sizes, in the launch configuration the benchmark
-times (128^3 image, K=5, C=8, B=2, J=491,520, W=4, sigma=1.25; and the
-200x200x160, C=32, B=8, J=2,048,000 whole-brain workload).
+"""Parity at the full workload sizes, in the launch configurations the benchmark
+times (128^3 image, K=5, C=8, B=2, J=491,520, W=4, sigma=1.25, with the default
+kernel shapes and with the autotuned shapes the benchmark picks; and the
+200x200x160, C=32, J=2,048,000 whole-brain workload at coil minibatches of 2
+and 8).
 
 The oracle cannot afford every output at these sizes, so:
   - forward: a seeded sample of output k-space points, evaluated by the oracle
     one by one (its own deapodisation, FFT of the grid and W^3 interpolation);
-  - adjoint at 128^3: every voxel (oracle spread + inverse FFT + crop);
-  - adjoint at 200x200x160: the adjoint identity <A x, y> = <x, A^H y>, which
-    holds at any size;
+  - adjoint at 128^3 and at 200x200x160 with B=2: every voxel (oracle spread +
+    inverse FFT + crop);
+  - adjoint at 200x200x160 with B=8: the adjoint identity <A x, y> = <x, A^H y>,
+    which holds at any size;
   - repeatability: two identical calls give identical bits (no atomics in the
     data path).
-Tolerance: FP32_BOUND = 2e-5 relative L2 (the stated bound at W=4 is 2e-3).
+Tolerance: FP32_BOUND = 2e-5 relative L2 (the stated bound at W=4 is 2e-3), and
+every element within 10 x FP32_BOUND of the largest reference magnitude.
 """
 import numpy as np
 import pytest
@@ -19,9 +23,21 @@ torch = pytest.importorskip("torch")
 
 from oracle import nufft as O
 from paper_2408_02367_gb300 import synth
+from tests.test_gpu_parity import assert_close
 
 pytestmark = pytest.mark.gpu
 FP32_BOUND = 2e-5
+
+# Kernel shapes the benchmark's autotuner picks on the 128^3 workload (8 x 4 x 4 spread
+# bins, 8 lines per CTA in the fused axis-3 FFT kernels; the 256- and 1024-thread
+# interpolation CTAs are within 1% of each other, so both are covered).
+BENCH_TUNINGS = {
+    "default": None,
+    "tuned_i256": {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                   "interp_threads": 256},
+    "tuned_i1024": {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                    "interp_threads": 1024},
+}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,10 +52,6 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def rel(a, b):
-    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
-
-
 def oracle_forward_samples(geo, x, S, V, omega, frame, coil, sel):
     """Oracle y[j] of one coil at the sample indices `sel` only."""
     K = x.shape[0]
@@ -49,40 +61,44 @@ def oracle_forward_samples(geo, x, S, V, omega, frame, coil, sel):
 
 
 @pytest.fixture(scope="module")
-def vol128():
-    from paper_2408_02367_gb300 import op
+def vol128_inputs():
     w = synth.WORKLOADS["vol128_w4"]
     x, S, V, omega, frame = synth.make_problem(w)
-    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=w.batch)
     geo = O.Geometry(w.n, w.width, w.oversamp)
-    return w, A, geo, x, S, V, omega, frame
+    return w, geo, x, S, V, omega, frame
+
+
+@pytest.fixture(scope="module", params=sorted(BENCH_TUNINGS))
+def vol128(request, vol128_inputs):
+    from paper_2408_02367_gb300 import op
+    w, geo, x, S, V, omega, frame = vol128_inputs
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=w.batch,
+                         tuning=BENCH_TUNINGS[request.param])
+    yield request.param, w, A, geo, x, S, V, omega, frame
+    A.close()
 
 
 def test_vol128_forward_sampled_outputs(vol128):
-    w, A, geo, x, S, V, omega, frame = vol128
+    name, w, A, geo, x, S, V, omega, frame = vol128
     coils = np.array([6, 3], np.int32)
     y = A.forward(_t(x), _t(coils)).cpu().numpy()
     sel = np.sort(np.random.default_rng(0).choice(w.J, size=3000, replace=False))
     for b, c in enumerate(coils):
         ref = oracle_forward_samples(geo, x, S, V, omega, frame, int(c), sel)
-        e = rel(y[b, sel], ref)
-        print(f"vol128 forward coil {c}: rel {e:.2e}")
-        assert e < FP32_BOUND
+        assert_close(y[b, sel], ref, FP32_BOUND, f"vol128 {name} forward coil {c}")
 
 
 def test_vol128_adjoint_all_voxels(vol128):
-    w, A, geo, x, S, V, omega, frame = vol128
+    name, w, A, geo, x, S, V, omega, frame = vol128
     coils = np.array([1, 5], np.int32)
     r = synth.random_complex((2, w.J), 17)
     a = A.adjoint(_t(r), _t(coils)).cpu().numpy()
     ref = O.gridding_adjoint(geo, r, S, V, omega, frame, coils)
-    e = rel(a, ref)
-    print(f"vol128 adjoint: rel {e:.2e}")
-    assert e < FP32_BOUND
+    assert_close(a, ref, FP32_BOUND, f"vol128 {name} adjoint")
 
 
 def test_vol128_repeatable_bits(vol128):
-    w, A, geo, x, S, V, omega, frame = vol128
+    name, w, A, geo, x, S, V, omega, frame = vol128
     ci = _t(np.array([2, 7], np.int32))
     xt = _t(x)
     y1 = A.forward(xt, ci)
@@ -94,13 +110,20 @@ def test_vol128_repeatable_bits(vol128):
     assert A.status() == 0
 
 
-def test_vol200_batch8_forward_sampled_and_adjoint_identity():
+@pytest.fixture(scope="module")
+def vol200():
     from paper_2408_02367_gb300 import op
     w = synth.WORKLOADS["vol200_w4"]
     x, S, V, omega, frame = synth.make_problem(w)
-    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8)
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8, borrow_maps=False)
     geo = O.Geometry(w.n, w.width, w.oversamp)
     assert A.grid == (250, 250, 200)
+    yield w, A, geo, x, S, V, omega, frame
+    A.close()
+
+
+def test_vol200_batch8_forward_sampled_and_adjoint_identity(vol200):
+    w, A, geo, x, S, V, omega, frame = vol200
     coils = np.array([0, 5, 9, 14, 18, 23, 27, 31], np.int32)
     xt = _t(x)
     ci = _t(coils)
@@ -109,9 +132,7 @@ def test_vol200_batch8_forward_sampled_and_adjoint_identity():
     yc = y.cpu().numpy()
     for b in (0, 6):                                   # two of the eight batch entries
         ref = oracle_forward_samples(geo, x, S, V, omega, frame, int(coils[b]), sel)
-        e = rel(yc[b, sel], ref)
-        print(f"vol200 forward coil {coils[b]}: rel {e:.2e}")
-        assert e < FP32_BOUND
+        assert_close(yc[b, sel], ref, FP32_BOUND, f"vol200 B=8 forward coil {coils[b]}")
     r = _t(synth.random_complex((8, w.J), 23))
     AHr = A.adjoint(r, ci)
     lhs = torch.vdot(r.flatten().to(torch.complex128), y.flatten().to(torch.complex128))
@@ -120,3 +141,30 @@ def test_vol200_batch8_forward_sampled_and_adjoint_identity():
     print(f"vol200 adjoint identity: {ident:.2e}")
     assert ident < 1e-5
     assert A.status() == 0
+
+
+def test_vol200_batch2_adjoint_all_voxels(vol200):
+    """The whole-brain adjoint against the oracle at every voxel, for a minibatch of 2."""
+    w, A, geo, x, S, V, omega, frame = vol200
+    coils = np.array([30, 4], np.int32)
+    r = synth.random_complex((2, w.J), 29)
+    a = A.adjoint(_t(r), _t(coils)).cpu().numpy()
+    ref = O.gridding_adjoint(geo, r, S, V, omega, frame, coils)
+    assert_close(a, ref, FP32_BOUND, "vol200 B=2 adjoint")
+    assert A.status() == 0
+
+
+def test_borrowed_coil_maps_give_the_same_bits(vol200):
+    """SDP_FLAG_BORROW_MAPS: a plan reading the caller's coil maps equals the copying plan."""
+    from paper_2408_02367_gb300 import op
+    w, A, geo, x, S, V, omega, frame = vol200
+    St = _t(S)
+    Ab = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, St, max_batch=8, borrow_maps=True)
+    assert Ab.info()["total_bytes"] < A.info()["total_bytes"] - St.numel() * 8 + 1
+    ci = _t(np.array([3, 17], np.int32))
+    xt = _t(x)
+    y, yb = A.forward(xt, ci), Ab.forward(xt, ci)
+    assert torch.equal(y, yb)
+    assert torch.equal(A.adjoint(y, ci), Ab.adjoint(y, ci))
+    assert Ab.status() == 0
+    Ab.close()

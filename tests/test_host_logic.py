@@ -76,4 +76,62 @@ def test_bench_byte_model_and_oracle_scaling():
     assert set(sb) == {"fwd_prologue_fft3", "fwd_fft2", "fwd_fft1", "interp", "residual_loss", "spread",
                        "adj_ifft1", "adj_ifft2", "adj_ifft3_epilogue"}
     assert sb["fwd_fft1"] == 8 * 2 * 5 * (128 * 160 * 160 + 160 ** 3)
-    assert math.isclose(bench.oracle_step_seconds(w, 2, 1.0, 0.5, w.J // 4), 2 * 5 * (1.0 + 2.0))
+
+
+def test_bench_oracle_pieces_sum_to_the_oracle_step():
+    """The CPU baseline splits a step into (coil, channel) pieces of the oracle's own steps; their
+    sum over channels is the oracle's gridding forward, and the pool runs whole steps."""
+    import bench
+    from oracle import nufft as O
+    w = synth.Workload("tiny", (8, 10, 6), 3, 3, 4, 1, 64, 4, 2.0, 2)
+    x, S, V, omega, frame = synth.make_problem(w)
+    bench._oracle_init(w.n, w.width, w.oversamp, x, S, V, omega, frame)
+    geo = O.Geometry(w.n, w.width, w.oversamp)
+    for c in (0, 2):
+        y = sum(bench._oracle_fwd(c, k) for k in range(w.K))
+        ref = O.gridding_forward(geo, x, S, V, omega, frame, [c])[0]
+        assert np.allclose(y, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+        r = synth.random_complex(w.J, 5).astype(np.complex128)
+        chk = sum(bench._oracle_adj(c, k, r) for k in range(w.K))
+        ref_a = O.gridding_adjoint(geo, r[None], S, V, omega, frame, [c])
+        assert abs(chk - ref_a.sum()) <= 1e-10 * np.abs(ref_a).sum()
+    orc = bench.OracleSteps(w, 2, max_workers=2)
+    try:
+        ts = orc.time_steps([np.array([0, 2]), np.array([1, 0])])
+    finally:
+        orc.close()
+    assert len(ts) == 2 and all(t > 0 for t in ts)
+    line = bench.oracle_line(w, 2, ts, 2, "test")
+    assert line["cores"] == 2 and math.isclose(line["value"], 2 * w.J / np.mean(ts))
+
+
+def test_multi_volume_and_whole_brain_shapes():
+    """The six-volume batch and the whole-brain minibatches: sizes, grids and coil minibatches C/4."""
+    grids = {"mv64": (80, 80, 80), "mv96": (120, 120, 120), "mv128": (160, 160, 160),
+             "mv128x96": (160, 160, 120), "mv160": (200, 200, 200), "mv200x160": (250, 250, 200)}
+    from oracle import nufft as O
+    for w in synth.MULTI_VOLUME:
+        assert w.batch == w.C // 4 and w.arm_len == 1024 and w.arms == 1 and w.K == 5
+        assert O.Geometry(w.n, w.width, w.oversamp).M == grids[w.name]
+    assert [w.C for w in synth.MULTI_VOLUME] == [8, 8, 16, 16, 32, 32]
+    assert synth.WHOLE_BRAIN_BATCHES == (1, 2, 4, 8)
+
+
+def test_separable_coil_maps_equal_their_elementwise_definition():
+    """coil_maps builds each map as an outer product of 1-D profiles; it must equal the map written
+    per voxel (Gaussian bump at a Fibonacci-sphere direction, linear phase ramp, unit RSS)."""
+    n, C = (9, 12, 7), 5
+    S = synth.coil_maps(n, C)
+    c1, c2, c3 = [(np.arange(d) - d // 2) / (d / 2.0) for d in n]
+    X, Y, Z = np.meshgrid(c1, c2, c3, indexing="ij")
+    ga = np.pi * (3.0 - math.sqrt(5.0))
+    ref = np.empty((C,) + n, np.complex128)
+    for c in range(C):
+        zc = 1.0 - 2.0 * (c + 0.5) / C
+        rc = math.sqrt(max(0.0, 1.0 - zc * zc))
+        d = np.array([rc * math.cos(ga * c), rc * math.sin(ga * c), zc]) * 1.2
+        mag = np.exp(-((X - d[0]) ** 2 + (Y - d[1]) ** 2 + (Z - d[2]) ** 2) / (2.0 * 1.44))
+        ref[c] = mag * np.exp(1j * (2.0 * np.pi * c / C + 0.3 * (d[0] * X + d[1] * Y + d[2] * Z)))
+    ref /= np.sqrt(np.sum(np.abs(ref) ** 2, axis=0))[None]
+    assert np.max(np.abs(S - ref)) < 1e-6
+    assert np.allclose(np.sum(np.abs(S.astype(np.complex128)) ** 2, axis=0), 1.0, atol=1e-6)
