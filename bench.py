@@ -430,6 +430,16 @@ def _plain_step(A, torch, x, y_meas, ci, K):
     return y_p, loss, g
 
 
+WHOLE_BRAIN_CANDIDATES = [
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024},
+    {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
+     "spread_coils": 1},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 1024, "fft_engine": 0, "fft_lines": 4, "interp_threads": 256},
+]
+
+
 def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
     """200x200x160, C=32, J=2,048,000: the graph-captured DIP step at each coil minibatch B in {1,2,4,8}
     (against the plain form at equal accuracy), and the work list of four items (own TSMI each, B=1,2,4,8)
@@ -437,10 +447,19 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
     from paper_2408_02367_gb300 import graph as sdp_graph
     w = synth.WORKLOADS["vol200_w4"]
     Bmax = max(synth.WHOLE_BRAIN_BATCHES)
+    # the plan's workspace holds the whole work list's coils (1 + 2 + 4 + 8), so the batched
+    # calls run every item in the same launches
+    Bplan = sum(synth.WHOLE_BRAIN_BATCHES)
     t0 = time.perf_counter()
     x_true, S, V, omega, frame = synth.make_problem(w)
     synth_s = time.perf_counter() - t0
-    A, plan_s = _upload_plan(op, torch, w, omega, frame, V, S, Bmax, dev, tuning)
+    tune_table = None
+    if not args.no_tune:
+        # kernel shapes for this workload, by the autotuner on its own trajectory at B = 8
+        from paper_2408_02367_gb300 import tune
+        tuning, tune_table = tune.autotune(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=Bmax, B=Bmax,
+                                           cands=WHOLE_BRAIN_CANDIDATES, reps=3, device=dev)
+    A, plan_s = _upload_plan(op, torch, w, omega, frame, V, S, Bplan, dev, tuning)
     del S
     info = A.info()
     M = (info["M1"], info["M2"], info["M3"])
@@ -449,7 +468,8 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
     nsteps = min(args.steps, 20)
     rows = {"workload": workload_desc(w, Bmax).replace(f", coil minibatch B={Bmax}", ""), "grid": list(M),
             "plan_create_s": plan_s, "synth_inputs_s": synth_s, "plan_device_bytes": info["total_bytes"],
-            "workspace_bytes": info["workspace_bytes"], "incidences": info["ninc"], "per_batch": {}}
+            "workspace_bytes": info["workspace_bytes"], "incidences": info["ninc"], "per_batch": {},
+            "tuning": dict(A.tuning, spread_bins=list(A.tuning["spread_bins"])), "autotuner": tune_table}
     for B in synth.WHOLE_BRAIN_BATCHES:
         draws = synth.coil_minibatches(w.C, B, nsteps + args.warmup, seed=synth.SEED_COILS_DRAW + 100 + B)
         coil_dev = torch.from_numpy(np.stack(draws)).to(dev)
@@ -525,6 +545,10 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
     return rows
 
 
+def mv_tuning_desc(A):
+    return dict(A.tuning, spread_bins=list(A.tuning["spread_bins"]))
+
+
 def multi_volume_rows(args, torch, op, dev, tuning, flush, hbm):
     """Six independent reconstructions of different matrix sizes (64^3 .. 200x200x160, C in {8,16,32}):
     one DIP step of every volume (coil minibatch C/4 each) as one batched forward, a residual/loss per
@@ -568,10 +592,23 @@ def multi_volume_rows(args, torch, op, dev, tuning, flush, hbm):
     set_draw(0)
     dip_step_all()
     torch.cuda.synchronize()
-    # eager, then captured once and replayed
+    # eager (stage times of the batched launches recorded on the first plan), then the same
+    # batch on the library's older path for comparison: each plan's nine launches on worker streams
+    neager = min(args.steps, 10)
     n0 = op.launch_count()
-    eager_ms = _events_ms(torch, lambda i: (set_draw(args.warmup + i), dip_step_all()), min(args.steps, 10), flush)
-    eager_launches = (op.launch_count() - n0) / min(args.steps, 10)
+    plans[0].profile(True)
+    plans[0].profile_read()
+    eager_ms = _events_ms(torch, lambda i: (set_draw(args.warmup + i), dip_step_all()), neager, flush)
+    prof = plans[0].profile_read()
+    plans[0].profile(False)
+    eager_launches = (op.launch_count() - n0) / neager
+    stage_ms = {k: v[0] / neager for k, v in prof.items() if v[1] > 0 and k != "residual_loss"}
+    os.environ["SDP_BATCH_STREAMS"] = "1"
+    try:
+        dip_step_all()
+        streams_ms = _events_ms(torch, lambda i: (set_draw(args.warmup + i), dip_step_all()), neager, flush)
+    finally:
+        del os.environ["SDP_BATCH_STREAMS"]
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
@@ -593,7 +630,10 @@ def multi_volume_rows(args, torch, op, dev, tuning, flush, hbm):
     nsamp = sum(it["w"].batch * it["w"].J for it in items)
     model = sum(path_model_bytes(it["w"], it["w"].batch, it["M"]) for it in items)
     out = {"volumes": rows, "setup_s": setup_s,
-           "dip_step_all_volumes_ms": {"cuda_graph": graph_ms, "eager": eager_ms},
+           "dip_step_all_volumes_ms": {"cuda_graph": graph_ms, "eager": eager_ms,
+                                       "eager_plan_by_plan_on_worker_streams": streams_ms},
+           "batched_stage_ms_per_step": stage_ms,
+           "tuning": mv_tuning_desc(items[0]["A"]),
            "nu_samples_per_s": nsamp / (graph_ms * 1e-3),
            "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (graph_ms * 1e-3)},
            "launches_per_step": {"graph": graph_launches, "eager": eager_launches}}
@@ -831,7 +871,9 @@ def run_native(args):
     scale = {}
     if not args.no_scale_rows:
         scale["whole_brain"] = whole_brain_rows(args, torch, op, dev, tuning, flush, hbm)
-        scale["multi_volume"] = multi_volume_rows(args, torch, op, dev, tuning, flush, hbm)
+        # the six volumes share the whole-brain workload's kernel width and channels: its tuning
+        mv_tuning = dict(scale["whole_brain"]["tuning"]) if not args.no_tune else None
+        scale["multi_volume"] = multi_volume_rows(args, torch, op, dev, mv_tuning, flush, hbm)
 
     # ---- rows built on the operator: DCF estimation, SVD-MRF initialiser, CG iteration ----
     from paper_2408_02367_gb300 import recon

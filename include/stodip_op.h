@@ -138,14 +138,19 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 or 8 for lengths >= 240), 8 or 4 (fewer lines: more, smaller
  *                 CTAs, so more of them resident per SM).
  *   fft_cols      grid columns per CTA of the strided axis-1 and axis-2 FFT
- *                 passes: 0 (default: 16, or 8 for lengths >= 240), 32 (lengths
- *                 up to 160; longer axes keep the default) or 8.
+ *                 passes: 0 (default: 16), 32 (lengths up to 160; longer axes
+ *                 keep the default) or 8.
  *   interp_threads  threads per CTA of the persistent interpolation kernel:
- *                 0 (default: 1024 for W <= 4, else 256), 256 or 1024 (W <= 4
- *                 only, else SDP_ERR_UNSUPPORTED).  1024 puts one CTA on an SM,
- *                 whose warps then gather for consecutive samples and share
- *                 the SM's L1; 256 leaves more registers per thread, so more
- *                 gathers in flight per warp.
+ *                 0 (default: 256), 256 or 1024 (W <= 4 only, else
+ *                 SDP_ERR_UNSUPPORTED).  1024 puts one CTA on an SM, whose
+ *                 warps then gather for consecutive samples and share the SM's
+ *                 L1; it can pay for a minibatch of one or two coils and loses
+ *                 badly for eight (the L1 holds fewer coils' windows).
+ *   spread_coils  coils of the minibatch one spread warp accumulates: 0 (default:
+ *                 two where the doubled register columns fit, i.e. 4-deep bins
+ *                 with at most 5 channels per group, else one), 1 or 2 (2 falls
+ *                 back to one where it does not fit).  Two coils share one
+ *                 staging of each incidence's positions, weights and coverage.
  */
 typedef struct {
     int32_t spread_bins[3];
@@ -154,6 +159,7 @@ typedef struct {
     int32_t fft_lines;
     int32_t fft_cols;
     int32_t interp_threads;
+    int32_t spread_coils;
 } sdp_tuning;
 
 /*
@@ -295,14 +301,30 @@ typedef struct {
 /*
  * Apply the forward (resp. adjoint) operator of every item (StoDIP Eq. 3 for
  * several reconstructions at once, e.g. uneven coil minibatches of volumes of
- * different matrix sizes).  Items whose plans differ run concurrently on
- * library-owned worker streams forked from and joined back to `stream`, so the
- * whole batch is ordered after earlier work on `stream` and before later work
- * on it, and can be captured in a CUDA graph; items that share a plan run one
- * after the other (they share its workspace).  All items are checked before
- * anything is launched.  The worker streams of a device are created by its
- * first batched call: make that call before any stream capture.  Batched calls
- * from several host threads are serialised by the library.
+ * different matrix sizes).  All items are checked before anything is launched.
+ *
+ * One launch per stage: when every item's plan has the same kernel width W
+ * (4 or 6), channel count K (K <= 8 and K <= 32 / W), spread bin depth and
+ * interpolation CTA size, and every grid length has a two-pass FFT (48, 64,
+ * 80, 96, 100, 120, 128, 160, 200, 240, 250, 256), the whole batch is one
+ * launch per stage: 4 for the forward (prologue + axis-3 FFT, axis-2 FFT,
+ * axis-1 FFT, interpolation), 4 for the adjoint (spread, inverse axis-1 and
+ * axis-2 FFTs, axis-3 FFT + epilogue), each covering the work of every item.
+ * Items that share a plan take consecutive coil slices of its workspace; when
+ * their minibatches together exceed its max_batch, or when an item's output
+ * overlaps the output of an earlier item of the batch (e.g. two adjoints
+ * adding into one image), the batch runs in waves of such launch sets, in item
+ * order.  These launches are on `stream` itself.  Up to 16 items per wave.
+ *
+ * Otherwise (or with the environment variable SDP_BATCH_STREAMS set) each
+ * item runs its own launches: items whose plans differ run concurrently on
+ * library-owned worker streams forked from and joined back to `stream`, items
+ * that share a plan one after the other.  The worker streams of a device are
+ * created by its first such call: make that call before any stream capture.
+ *
+ * Either way the whole batch is ordered after earlier work on `stream` and
+ * before later work on it, and can be captured in a CUDA graph.  Batched
+ * calls from several host threads are serialised by the library.
  */
 int sdp_forward_batched(const sdp_work* items, int32_t n, void* stream);
 int sdp_adjoint_batched(const sdp_work* items, int32_t n, void* stream);

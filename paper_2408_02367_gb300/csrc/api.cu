@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "batch.cuh"
 #include "sdp_internal.cuh"
 
 using namespace sdp;
@@ -44,6 +45,7 @@ struct sdp_plan_s {
     int nb[3] = {0, 0, 0};
     int spread_chunk = 0;
     int interp_threads = 0;   // resolved CTA size of the interpolation kernel
+    int spread_coils = 0;     // coils per spread warp: 0 = two where they fit, 1 = one
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -210,7 +212,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     // interpolation CTA size: the 1024-thread kernel is built for W <= 4 only
     const int ithreads = tn ? tn->interp_threads : 0;
     if (ithreads == 1024 && W > 4) return SDP_ERR_UNSUPPORTED;
-    p->interp_threads = ithreads ? ithreads : (W <= 4 ? 1024 : 256);
+    p->interp_threads = ithreads ? ithreads : 256;
+    p->spread_coils = tn ? tn->spread_coils : 0;
 
     // ---- host tables ----
     std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
@@ -512,7 +515,7 @@ int adjoint_impl(sdp_plan_s* p, const void* y, const int32_t* coil_idx, int B, i
     SDP_TRY(run(p, ST_SPREAD, st, [&] {
         return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->wts, p->V,
                              static_cast<const float2*>(y), scale, B, k0, nk, p->bufA, p->partials, p->slots_per_b,
-                             p->counters, p->nbins, st);
+                             p->counters, p->nbins, p->spread_coils, st);
     }));
     SDP_TRY(run(p, ST_ADJ_FFT1, st, [&] {
         return launch_fft_strided(p->ax[0], 1, p->bufA, p->bufB, (int)M1, 0, (int)N1, 1, M2 * M3 * nk, B, st);
@@ -559,6 +562,190 @@ int worker_pool(WorkerPool** out) {
     return SDP_OK;
 }
 
+// ---- batched calls in one launch per stage (batch.cu) ----
+
+// Whether the items can share launches: the same kernel width, channel count,
+// spread bin depth and interpolation CTA size; one channel group (K <= 8 and
+// K <= 32 / W); every grid length served by the two-pass FFT.
+bool fused_eligible(const sdp_work* items, int n) {
+    if (n < 1) return false;
+    const sdp_plan_s* p0 = items[0].plan;
+    for (int i = 0; i < n; ++i) {
+        const sdp_plan_s* p = items[i].plan;
+        if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[2] != p0->bs[2] ||
+            p->interp_threads != p0->interp_threads)
+            return false;
+        if (p->geo.K > 8 || p->geo.K > 32 / p->geo.W || !mv_width_supported(p->geo.W)) return false;
+        for (int a = 0; a < 3; ++a)
+            if (p->ax[a].generic || !mv_length_supported(p->geo.M[a])) return false;
+    }
+    return true;
+}
+
+// One wave: items whose plans have room for all their coils at once.  Fills
+// the launch descriptors and runs the four stages of one direction.
+int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vector<int>& coil_off, bool adjoint,
+             cudaStream_t st) {
+    MvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int n = (int)idx.size();
+    const sdp_plan_s* p0 = items[idx[0]].plan;
+    for (int q = 0; q < n; ++q) {
+        const sdp_work& w = items[idx[q]];
+        sdp_plan_s* p = w.plan;
+        const Geo& g = p->geo;
+        MvItem& it = a.it[q];
+        const long long N1 = g.N[0], N2 = g.N[1];
+        const long long M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+        const long long K = g.K;
+        const size_t gridA = (size_t)std::max<long long>(M1 * M2 * M3, N1 * N2 * M3);
+        const size_t gridB = (size_t)(N1 * M2 * M3);
+        it.g = g;
+        for (int d = 0; d < 3; ++d) {
+            it.L[d] = g.M[d];
+            it.tw[d] = p->ax[d].tw;
+            it.d[d] = dinv_axis(p, d);
+        }
+        it.S = p->S;
+        it.coil_idx = w.coil_idx;
+        it.B = w.B;
+        it.accumulate = w.accumulate ? 1 : 0;
+        it.status = p->status;
+        it.bufA = p->bufA + (size_t)coil_off[q] * gridA * K;
+        it.bufB = p->bufB + (size_t)coil_off[q] * gridB * K;
+        it.pts = p->pts;
+        it.tframe = p->tframe;
+        it.wts = p->wts;
+        it.V = p->V;
+        if (adjoint) {
+            it.x = static_cast<float2*>(w.out);
+            it.pass[0] = MvPass{it.bufA, it.bufB, (int)M1, 0, (int)N1, 1, M2 * M3 * K};
+            it.pass[1] = MvPass{it.bufB, it.bufA, (int)M2, 0, (int)N2, 1, M3 * K};
+        } else {
+            it.x = const_cast<float2*>(static_cast<const float2*>(w.in));
+            it.y = static_cast<float2*>(w.out);
+            it.pass[1] = MvPass{it.bufA, it.bufB, (int)N2, 1, (int)M2, 0, M3 * K};
+            it.pass[0] = MvPass{it.bufB, it.bufA, (int)N1, 1, (int)M1, 0, M2 * M3 * K};
+        }
+        SpreadArgs& sa = it.sa;
+        sa.g = g;
+        sa.bs1 = p->bs[0];
+        sa.bs2 = p->bs[1];
+        sa.bs3 = p->bs[2];
+        sa.nb1 = p->nb[0];
+        sa.nb2 = p->nb[1];
+        sa.nb3 = p->nb[2];
+        sa.subs = p->subs;
+        sa.inc = p->inc;
+        sa.pts = p->pts;
+        sa.tframe = p->tframe;
+        sa.wts = p->wts;
+        sa.V = p->V;
+        sa.y = adjoint ? static_cast<const float2*>(w.in) : nullptr;
+        sa.scale = nullptr;
+        sa.k0 = 0;
+        sa.nk = g.K;
+        sa.grids = it.bufA;
+        sa.slot_elems = (long long)g.K * p->bs[0] * p->bs[1] * p->bs[2];
+        sa.partials = p->partials + (size_t)coil_off[q] * (size_t)p->slots_per_b * (size_t)sa.slot_elems;
+        sa.slots_per_b = p->slots_per_b;
+        sa.counters = p->counters + (size_t)coil_off[q] * (size_t)p->nbins;
+        sa.nbins = p->nbins;
+        sa.ngroups = 1;
+        sa.group = 0;
+        it.nsub = p->nsub;
+        it.spread_pairs = (spread_pairs_fit(p->bs[2], g.K) && p->spread_coils != 1 && w.B >= 2) ? 1 : 0;
+    }
+    // units of each stage
+    auto units = [&](auto count) {
+        MvUnits u;
+        u.n = n;
+        u.start[0] = 0;
+        for (int q = 0; q < n; ++q) u.start[q + 1] = u.start[q] + count(a.it[q]);
+        return u;
+    };
+    auto ceil_div = [](long long x, long long y) { return (x + y - 1) / y; };
+    const MvUnits u_fused_fwd = units([&](const MvItem& it) {
+        return ceil_div((long long)it.g.N[0] * it.g.N[1] * it.g.K, mv_fused_lines(it.L[2])) * it.B;
+    });
+    const MvUnits u_fused_adj = units([&](const MvItem& it) {
+        return ceil_div((long long)it.g.N[0] * it.g.N[1] * it.g.K, mv_fused_lines(it.L[2]));
+    });
+    auto u_strided = [&](int axis) {
+        return units([&](const MvItem& it) {
+            const long long outer = axis == 1 ? (long long)it.B * it.g.N[0] : (long long)it.B;
+            return ceil_div(it.pass[axis].inner, mv_strided_cols(it.L[axis])) * outer;
+        });
+    };
+    // stage timing (sdp_profile_*) is recorded on the first item's plan
+    sdp_plan_s* pf = items[idx[0]].plan;
+    if (!adjoint) {
+        const MvUnits u2 = u_strided(1), u1 = u_strided(0);
+        const MvUnits us = units([&](const MvItem& it) { return (long long)it.g.J; });
+        SDP_TRY(run(pf, ST_FWD_FFT3, st, [&] { return launch_mv_prologue(a, u_fused_fwd, st); }));
+        SDP_TRY(run(pf, ST_FWD_FFT2, st, [&] { return launch_mv_strided(a, u2, 1, 0, st); }));
+        SDP_TRY(run(pf, ST_FWD_FFT1, st, [&] { return launch_mv_strided(a, u1, 0, 0, st); }));
+        SDP_TRY(run(pf, ST_INTERP, st, [&] { return launch_mv_interp(a, us, p0->geo.W, p0->interp_threads, st); }));
+    } else {
+        const MvUnits u1 = u_strided(0), u2 = u_strided(1);
+        const MvUnits usp = units([&](const MvItem& it) {
+            return (long long)it.nsub * (it.spread_pairs ? (it.B + 1) / 2 : it.B);
+        });
+        SDP_TRY(run(pf, ST_SPREAD, st, [&] { return launch_mv_spread(a, usp, p0->bs[2], p0->geo.W, p0->geo.K, st); }));
+        SDP_TRY(run(pf, ST_ADJ_FFT1, st, [&] { return launch_mv_strided(a, u1, 0, 1, st); }));
+        SDP_TRY(run(pf, ST_ADJ_FFT2, st, [&] { return launch_mv_strided(a, u2, 1, 1, st); }));
+        SDP_TRY(run(pf, ST_ADJ_FFT3, st, [&] { return launch_mv_epilogue(a, u_fused_adj, st); }));
+    }
+    return SDP_OK;
+}
+
+// Bytes an item writes: y [B][J] (forward) or out [K][N1][N2][N3] (adjoint).
+std::pair<uintptr_t, uintptr_t> out_range(const sdp_work& w, bool adjoint) {
+    const sdp_plan_s* p = w.plan;
+    const size_t n = adjoint ? (size_t)p->geo.K * p->n[0] * p->n[1] * p->n[2] : (size_t)w.B * p->geo.J;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(w.out);
+    return {a, a + n * sizeof(float2)};
+}
+
+// Items in order; an item joins the current wave while its plan has room for
+// its coils there (items of one plan take consecutive coil slices of the
+// plan's workspace) and its output does not overlap the output of an item
+// already in the wave (two items adding into one image must not run in the
+// same launch), else the wave is run and a new one starts.
+int run_batched_fused(const sdp_work* items, int n, bool adjoint, cudaStream_t st) {
+    std::vector<int> idx, off;
+    std::vector<std::pair<const sdp_plan_s*, int>> used;   // coils taken per plan in the wave
+    for (int i = 0; i < n; ++i) {
+        const sdp_plan_s* p = items[i].plan;
+        int* u = nullptr;
+        for (auto& e : used)
+            if (e.first == p) u = &e.second;
+        const int have = u ? *u : 0;
+        const auto ri = out_range(items[i], adjoint);
+        bool overlap = false;
+        for (int q : idx) {
+            const auto rq = out_range(items[q], adjoint);
+            overlap |= ri.first < rq.second && rq.first < ri.second;
+        }
+        if ((int)idx.size() == kMaxMvItems || have + items[i].B > p->maxB || overlap) {
+            SDP_TRY(run_wave(items, idx, off, adjoint, st));
+            idx.clear();
+            off.clear();
+            used.clear();
+            u = nullptr;
+        }
+        if (!u) {
+            used.emplace_back(p, 0);
+            u = &used.back().second;
+        }
+        idx.push_back(i);
+        off.push_back(*u);
+        *u += items[i].B;
+    }
+    if (!idx.empty()) SDP_TRY(run_wave(items, idx, off, adjoint, st));
+    return SDP_OK;
+}
+
 int run_batched(const sdp_work* items, int n, bool adjoint, cudaStream_t st) {
     if (n < 0 || (n > 0 && !items)) return SDP_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
@@ -567,6 +754,7 @@ int run_batched(const sdp_work* items, int n, bool adjoint, cudaStream_t st) {
         SDP_TRY(check_call(w.plan, w.in, w.coil_idx, w.B, 0, w.plan->geo.K, w.out));
     }
     if (n == 0) return SDP_OK;
+    if (fused_eligible(items, n) && !std::getenv("SDP_BATCH_STREAMS")) return run_batched_fused(items, n, adjoint, st);
     auto run_one = [&](const sdp_work& w, cudaStream_t s) {
         return adjoint ? adjoint_impl(w.plan, w.in, w.coil_idx, w.B, 0, w.plan->geo.K, w.out, w.accumulate ? 1 : 0,
                                       nullptr, s)
@@ -631,7 +819,8 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
         if (tn->spread_chunk < 32 || tn->spread_chunk > 65536 || tn->fft_engine < 0 || tn->fft_engine > 1 ||
             (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) ||
             (tn->fft_cols != 0 && tn->fft_cols != 32 && tn->fft_cols != 8) ||
-            (tn->interp_threads != 0 && tn->interp_threads != 256 && tn->interp_threads != 1024))
+            (tn->interp_threads != 0 && tn->interp_threads != 256 && tn->interp_threads != 1024) ||
+            tn->spread_coils < 0 || tn->spread_coils > 2)
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -726,7 +915,7 @@ int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* st
     SDP_TRY(run(p, ST_SPREAD, st, [&] {
         return launch_spread(g, p->bs, p->nb, p->subs, p->nsub, p->inc, p->pts, p->tframe, p->wts, p->V,
                              static_cast<const float2*>(y), nullptr, B, 0, g.K, p->bufA, p->partials, p->slots_per_b,
-                             p->counters, p->nbins, st);
+                             p->counters, p->nbins, p->spread_coils, st);
     }));
     return run(p, ST_INTERP, st, [&] {
         return launch_interp(g, p->interp_threads, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K,
@@ -784,6 +973,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->fft_lines = p->ax[2].lines;
     out->fft_cols = p->ax[0].cols;
     out->interp_threads = p->interp_threads;
+    out->spread_coils = p->spread_coils;
     return SDP_OK;
 }
 

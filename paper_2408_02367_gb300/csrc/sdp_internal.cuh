@@ -66,6 +66,34 @@ struct Geo {
     float halfW;
 };
 
+// Arguments of the spread kernels (spread_impl.cuh) for one plan and call.
+struct SpreadArgs {
+    Geo g;
+    int bs1, bs2, bs3;
+    int nb1, nb2, nb3;
+    const SubProb* subs;
+    const int* inc;
+    const float4* pts;
+    const int* tframe;
+    const float* wts;
+    const float2* V;
+    const float2* y;
+    const float* scale;
+    int k0, nk;
+    float2* grids;
+    float2* partials;
+    long long slots_per_b;
+    long long slot_elems;
+    int* counters;
+    int nbins;
+    int ngroups;   // channel groups of this call (counters are per group)
+    int group;
+};
+
+// Whether one spread warp can hold the register columns of two coils (bins of depth
+// B3, NK channels in the group): 40 packed accumulator pairs at most.
+__host__ __device__ constexpr bool spread_pairs_fit(int B3, int NK) { return B3 * NK <= 20; }
+
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
 // Spread bin shapes with a kernel: 8 x 4 x 8 and 8 x 4 x 4 grid points.
 bool spread_bins_supported(const int bs[3]);
@@ -89,7 +117,8 @@ cudaError_t launch_interp(const Geo& g, int threads, const float4* pts, const in
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
                           const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
-                          float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st);
+                          float2* partials, long long slots_per_b, int* counters, int nbins, int coils,
+                          cudaStream_t st);
 long long residual_loss_partials(int maxB, long long J);
 cudaError_t launch_residual_loss(const float2* yhat, const float2* ymeas, const int* meas_idx, const float* dcf, int B,
                                  long long J, int nrows, float2* r2, double* partials, unsigned int* counter,

@@ -34,29 +34,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-struct SpreadArgs {
-    Geo g;
-    int bs1, bs2, bs3;
-    int nb1, nb2, nb3;
-    const SubProb* subs;
-    const int* inc;
-    const float4* pts;
-    const int* tframe;
-    const float* wts;
-    const float2* V;
-    const float2* y;
-    const float* scale;
-    int k0, nk;
-    float2* grids;
-    float2* partials;
-    long long slots_per_b;
-    long long slot_elems;
-    int* counters;
-    int nbins;
-    int ngroups;   // channel groups of this call (counters are per group)
-    int group;
-};
-
 // Bins are 8 x 4 x B3 grid points (axis 1 x axis 2 x axis 3; B3 = 8 or 4).
 // Lane l of the warp owns the axis-3 column (x1, x2) = (l / 4, l % 4) of the
 // bin: its B3 points x NK channels are accumulated in REGISTERS, so there is no shared
@@ -124,28 +101,32 @@ __device__ __forceinline__ void store_bin(float4* tr, const unsigned long long (
     }
 }
 
-template <int B3, int W, int NK>
-__global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
+// One warp's unit: subproblem `sub` for coils NC * by .. NC * by + NC - 1 (those below B).
+template <int B3, int W, int NK, int NC>
+__device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B, int sub, int by) {
     constexpr int BP = B1 * B2 * B3;
     constexpr int NW = 3 * W;
     constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
     // staging of 32 incidences, reused for the bin's store once they are summed; the
     // channel coefficients of an incidence sit at an even stride NKP so that they, like
-    // the B3 (w3, w3) pairs, are read 16 bytes at a time
+    // the B3 (w3, w3) pairs, are read 16 bytes at a time.  With NC = 2 the warp spreads
+    // two coils of the minibatch: the positions, weights and coverage of an incidence are
+    // staged once and serve both, only the coefficients conj(V[t, k]) r_b are per coil.
     constexpr int NKP = (NK + 1) & ~1;
-    constexpr int kStage = 32 * B3 * 8 + 32 * NKP * 8 + 32 * NP * 4 + 32 * 4;
+    constexpr int kStage = 32 * B3 * 8 + NC * 32 * NKP * 8 + 32 * NP * 4 + 32 * 4;
     constexpr int kTr = 32 * ((B3 * NK / 2) | 1) * 16;
     __shared__ __align__(16) unsigned char sraw[kStage > kTr ? kStage : kTr];
     float2* p3sm = reinterpret_cast<float2*>(sraw);  // [incidence][x3]: (w3, w3), 0 outside the window
-    float2* csm = p3sm + 32 * B3;                      // [incidence][k]: conj(V[t, k]) r
-    float* psm = reinterpret_cast<float*>(csm + 32 * NKP);  // [incidence][x1 (8) | x2 (4)], 0 outside
+    float2* csm = p3sm + 32 * B3;                      // [coil][incidence][k]: conj(V[t, k]) r_b
+    float* psm = reinterpret_cast<float*>(csm + NC * 32 * NKP);  // [incidence][x1 (8) | x2 (4)], 0 outside
     unsigned* msm = reinterpret_cast<unsigned*>(psm + 32 * NP);   // axis-3 positions covered (bit x3)
     float4* tr = reinterpret_cast<float4*>(sraw);
     const Geo& g = a.g;
     const int lane = threadIdx.x;
     const int x1 = lane >> 2, x2 = lane & 3;
-    const SubProb sp = a.subs[blockIdx.x];
-    const int b = blockIdx.y;
+    const SubProb sp = a.subs[sub];
+    const int b0 = by * NC;                            // first coil of the warp
+    const int nc = min(NC, B - b0);                    // its coils (the last warp of an odd batch has one)
     const int bin3 = sp.bin % a.nb3;
     const int bt = sp.bin / a.nb3;
     const int bin2 = bt % a.nb2;
@@ -155,13 +136,14 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     const long long G = (long long)M1 * M2 * M3;
 
     // accumulators as packed (Re, Im) pairs for the f32x2 multiply-adds
-    unsigned long long acc[B3][NK];
+    unsigned long long acc[NC][B3][NK];
 #pragma unroll
-    for (int x3 = 0; x3 < B3; ++x3)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int q = 0; q < NK; ++q) acc[x3][q] = 0ull;
+        for (int x3 = 0; x3 < B3; ++x3)
+#pragma unroll
+            for (int q = 0; q < NK; ++q) acc[c][x3][q] = 0ull;
 
-    const float2* yb = a.y + (long long)b * g.J;
     const float sc = a.scale ? __ldg(a.scale) : 1.f;
     const int kv = a.k0 + kofs;   // first channel of V of this group
     for (int base = 0; base < sp.count; base += 32) {
@@ -171,9 +153,6 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
             const float4 p = __ldg(a.pts + s);
             const int orig = __float_as_int(p.w);
             const int t = __ldg(a.tframe + s);
-            float2 r = __ldg(yb + orig);
-            r.x *= sc;
-            r.y *= sc;
             const float* ws = a.wts + (long long)s * NW;
             float wl[NW];
 #pragma unroll
@@ -217,10 +196,21 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
             }
             msm[lane] = mask;
             const float2* Vt = a.V + (long long)t * g.K + kv;
+            float2 vq[NK];
 #pragma unroll
-            for (int q = 0; q < NK; ++q) {
-                const float2 v = __ldg(Vt + q);
-                csm[lane * NKP + q] = make_float2(v.x * r.x + v.y * r.y, v.x * r.y - v.y * r.x);
+            for (int q = 0; q < NK; ++q) vq[q] = __ldg(Vt + q);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float2 r = make_float2(0.f, 0.f);   // a missing second coil spreads zeros and is not stored
+                if (c < nc) {
+                    r = __ldg(a.y + (long long)(b0 + c) * g.J + orig);
+                    r.x *= sc;
+                    r.y *= sc;
+                }
+#pragma unroll
+                for (int q = 0; q < NK; ++q)
+                    csm[(c * 32 + lane) * NKP + q] =
+                        make_float2(vq[q].x * r.x + vq[q].y * r.y, vq[q].x * r.y - vq[q].y * r.x);
             }
         }
         __syncwarp();
@@ -230,14 +220,17 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
             const float w12 = pw[x1] * pw[B1 + x2];
             unsigned long long w12p;
             asm("mov.b64 %0, {%1, %1};" : "=l"(w12p) : "f"(w12));
-            const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(csm + i * NKP);
             const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(p3sm + i * B3);
-            unsigned long long c[NK], wp3[B3];
+            unsigned long long cc[NC][NK], wp3[B3];
 #pragma unroll
-            for (int q = 0; q < NKP / 2; ++q) {
-                const ulonglong2 v = cp[q];
-                c[2 * q] = v.x;
-                if (2 * q + 1 < NK) c[2 * q + 1] = v.y;
+            for (int c = 0; c < NC; ++c) {
+                const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(csm + (c * 32 + i) * NKP);
+#pragma unroll
+                for (int q = 0; q < NKP / 2; ++q) {
+                    const ulonglong2 v = cp[q];
+                    cc[c][2 * q] = v.x;
+                    if (2 * q + 1 < NK) cc[c][2 * q + 1] = v.y;
+                }
             }
 #pragma unroll
             for (int x3 = 0; x3 < B3 / 2; ++x3) {
@@ -253,7 +246,10 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
                     unsigned long long w;
                     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(w) : "l"(w12p), "l"(wp3[x3]));
 #pragma unroll
-                    for (int q = 0; q < NK; ++q) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[x3][q]) : "l"(w), "l"(c[q]));
+                    for (int c = 0; c < NC; ++c)
+#pragma unroll
+                        for (int q = 0; q < NK; ++q)
+                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[c][x3][q]) : "l"(w), "l"(cc[c][q]));
                 }
             }
         }
@@ -263,61 +259,92 @@ __global__ void __launch_bounds__(32) spread_kernel(SpreadArgs a, int kofs) {
     // store: column (x1, x2) of the bin, element (x3, q) at gbin[x1 cs1 + x2 cs2 + x3 nk + q]
     const int nk = a.nk;
     const long long cs2 = (long long)M3 * nk, cs1 = (long long)M2 * cs2;
-    float2* gbin = a.grids + (long long)b * G * nk + (((long long)lo1 * M2 + lo2) * M3 + lo3) * nk + kofs;
+    float2* gbin0 = a.grids + (long long)b0 * G * nk + (((long long)lo1 * M2 + lo2) * M3 + lo3) * nk + kofs;
     const int n1 = M1 - lo1, n2 = M2 - lo2;
     const int x3end = min(B3, M3 - lo3);
     if (sp.nchunks == 1) {
-        store_bin<B3, NK>(tr, acc, gbin, cs1, cs2, n1, n2, x3end, nk, lane);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < nc)
+                store_bin<B3, NK>(tr, acc[c], gbin0 + (long long)c * G * nk, cs1, cs2, n1, n2, x3end, nk, lane);
         return;
     }
-    // multi-chunk bin: the chunk's partial tile in its slot, 16-byte pair j of lane l at
-    // [j][l] (each store instruction writes 512 contiguous bytes); the last chunk sums them
+    // multi-chunk bin: the chunk's partial tile of each coil in its slot, 16-byte pair j of
+    // lane l at [j][l] (each store instruction writes 512 contiguous bytes); the last chunk
+    // to arrive (one counter per bin and first coil of the warp) sums them
     constexpr int CQ = B3 * NK / 2;
-    float4* part = reinterpret_cast<float4*>(a.partials +
-                                             ((long long)b * a.slots_per_b + sp.slot + sp.chunk) * a.slot_elems +
-                                             (long long)kofs * BP);
 #pragma unroll
-    for (int j = 0; j < CQ; ++j)
-        part[j * 32 + lane] = pair4(acc[(2 * j) / NK][(2 * j) % NK], acc[(2 * j + 1) / NK][(2 * j + 1) % NK]);
+    for (int c = 0; c < NC; ++c) {
+        if (c < nc) {
+            float4* part = reinterpret_cast<float4*>(
+                a.partials + ((long long)(b0 + c) * a.slots_per_b + sp.slot + sp.chunk) * a.slot_elems +
+                (long long)kofs * BP);
+#pragma unroll
+            for (int j = 0; j < CQ; ++j)
+                part[j * 32 + lane] =
+                    pair4(acc[c][(2 * j) / NK][(2 * j) % NK], acc[c][(2 * j + 1) / NK][(2 * j + 1) % NK]);
+        }
+    }
     __threadfence();
     __syncwarp();
     int last = 0;
-    if (lane == 0)
-        last = (atomicAdd(a.counters + ((long long)b * a.ngroups + a.group) * a.nbins + sp.bin, 1) ==
-                sp.nchunks - 1);
+    int* counter = a.counters + ((long long)b0 * a.ngroups + a.group) * a.nbins + sp.bin;
+    if (lane == 0) last = (atomicAdd(counter, 1) == sp.nchunks - 1);
     last = __shfl_sync(kFull, last, 0);
     if (!last) return;
     __threadfence();
-    const float4* part0 = reinterpret_cast<const float4*>(
-        a.partials + ((long long)b * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP);
     const long long slot4 = a.slot_elems / 2;
 #pragma unroll
-    for (int j = 0; j < CQ; ++j) {
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int ch = 0; ch < sp.nchunks; ++ch) {
-            const float4 v = __ldcg(part0 + ch * slot4 + j * 32 + lane);
-            sum.x += v.x;
-            sum.y += v.y;
-            sum.z += v.z;
-            sum.w += v.w;
+    for (int c = 0; c < NC; ++c) {
+        if (c < nc) {
+            const float4* part0 = reinterpret_cast<const float4*>(
+                a.partials + ((long long)(b0 + c) * a.slots_per_b + sp.slot) * a.slot_elems + (long long)kofs * BP);
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) {
+                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int ch = 0; ch < sp.nchunks; ++ch) {
+                    const float4 v = __ldcg(part0 + ch * slot4 + j * 32 + lane);
+                    sum.x += v.x;
+                    sum.y += v.y;
+                    sum.z += v.z;
+                    sum.w += v.w;
+                }
+                acc[c][(2 * j) / NK][(2 * j) % NK] = pack2(sum.x, sum.y);
+                acc[c][(2 * j + 1) / NK][(2 * j + 1) % NK] = pack2(sum.z, sum.w);
+            }
+            store_bin<B3, NK>(tr, acc[c], gbin0 + (long long)c * G * nk, cs1, cs2, n1, n2, x3end, nk, lane);
         }
-        acc[(2 * j) / NK][(2 * j) % NK] = pack2(sum.x, sum.y);
-        acc[(2 * j + 1) / NK][(2 * j + 1) % NK] = pack2(sum.z, sum.w);
     }
-    store_bin<B3, NK>(tr, acc, gbin, cs1, cs2, n1, n2, x3end, nk, lane);
-    if (lane == 0) a.counters[((long long)b * a.ngroups + a.group) * a.nbins + sp.bin] = 0;
+    if (lane == 0) *counter = 0;
 }
 
+template <int B3, int W, int NK, int NC>
+__global__ void __launch_bounds__(32, NC * B3 * NK <= 20 ? 24 : (NC * B3 * NK <= 40 ? 16 : 1))
+spread_kernel(SpreadArgs a, int kofs, int B) {
+    spread_body<B3, W, NK, NC>(a, kofs, B, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// Coils per warp: two where the doubled accumulators fit (4-deep columns of at most 5
+// channels: 40 packed pairs), else one.
+template <int B3, int NK>
+__host__ __device__ constexpr int spread_coils() { return spread_pairs_fit(B3, NK) ? 2 : 1; }
+
 template <int B3, int W, int NK>
-cudaError_t launch_wk(const SpreadArgs& a, int kofs, int nsub, int B, cudaStream_t st) {
-    dim3 grid((unsigned)nsub, (unsigned)B);
-    spread_kernel<B3, W, NK><<<grid, 32, 0, st>>>(a, kofs);
+cudaError_t launch_wk(const SpreadArgs& a, int kofs, int nsub, int B, int coils, cudaStream_t st) {
+    constexpr int NC2 = spread_coils<B3, NK>();
+    if (NC2 == 2 && coils != 1 && B >= 2) {
+        dim3 grid((unsigned)nsub, (unsigned)((B + 1) / 2));
+        spread_kernel<B3, W, NK, NC2><<<grid, 32, 0, st>>>(a, kofs, B);
+    } else {
+        dim3 grid((unsigned)nsub, (unsigned)B);
+        spread_kernel<B3, W, NK, 1><<<grid, 32, 0, st>>>(a, kofs, B);
+    }
     return cudaGetLastError();
 }
 
 // Channels run in groups of at most 8 (one launch each, exact group size).
 template <int B3, int W>
-cudaError_t launch_w(SpreadArgs a, int nsub, int B, cudaStream_t st) {
+cudaError_t launch_w(SpreadArgs a, int nsub, int B, int coils, cudaStream_t st) {
     if (a.bs1 != B1 || a.bs2 != B2 || a.bs3 != B3) return cudaErrorInvalidValue;
     a.ngroups = (a.nk + 7) / 8;
     for (int gi = 0; gi < a.ngroups; ++gi) {
@@ -326,14 +353,14 @@ cudaError_t launch_w(SpreadArgs a, int nsub, int B, cudaStream_t st) {
         a.group = gi;
         cudaError_t e;
         switch (ng) {
-            case 1: e = launch_wk<B3, W, 1>(a, kofs, nsub, B, st); break;
-            case 2: e = launch_wk<B3, W, 2>(a, kofs, nsub, B, st); break;
-            case 3: e = launch_wk<B3, W, 3>(a, kofs, nsub, B, st); break;
-            case 4: e = launch_wk<B3, W, 4>(a, kofs, nsub, B, st); break;
-            case 5: e = launch_wk<B3, W, 5>(a, kofs, nsub, B, st); break;
-            case 6: e = launch_wk<B3, W, 6>(a, kofs, nsub, B, st); break;
-            case 7: e = launch_wk<B3, W, 7>(a, kofs, nsub, B, st); break;
-            default: e = launch_wk<B3, W, 8>(a, kofs, nsub, B, st); break;
+            case 1: e = launch_wk<B3, W, 1>(a, kofs, nsub, B, coils, st); break;
+            case 2: e = launch_wk<B3, W, 2>(a, kofs, nsub, B, coils, st); break;
+            case 3: e = launch_wk<B3, W, 3>(a, kofs, nsub, B, coils, st); break;
+            case 4: e = launch_wk<B3, W, 4>(a, kofs, nsub, B, coils, st); break;
+            case 5: e = launch_wk<B3, W, 5>(a, kofs, nsub, B, coils, st); break;
+            case 6: e = launch_wk<B3, W, 6>(a, kofs, nsub, B, coils, st); break;
+            case 7: e = launch_wk<B3, W, 7>(a, kofs, nsub, B, coils, st); break;
+            default: e = launch_wk<B3, W, 8>(a, kofs, nsub, B, coils, st); break;
         }
         if (e != cudaSuccess) return e;
         if (gi > 0) note_launches(1);   // the stage counts its first launch
@@ -345,7 +372,8 @@ template <int B3>
 cudaError_t launch_spread_depth(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,
                           const int* inc, const float4* pts, const int* tframe, const float* wts, const float2* V,
                           const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
-                          float2* partials, long long slots_per_b, int* counters, int nbins, cudaStream_t st) {
+                          float2* partials, long long slots_per_b, int* counters, int nbins, int coils,
+                          cudaStream_t st) {
     SpreadArgs a;
     a.g = g;
     a.bs1 = bs[0];
@@ -373,13 +401,13 @@ cudaError_t launch_spread_depth(const Geo& g, const int bs[3], const int nb[3], 
     a.ngroups = 1;
     a.group = 0;
     switch (g.W) {
-        case 2: return launch_w<B3, 2>(a, nsub, B, st);
-        case 3: return launch_w<B3, 3>(a, nsub, B, st);
-        case 4: return launch_w<B3, 4>(a, nsub, B, st);
-        case 5: return launch_w<B3, 5>(a, nsub, B, st);
-        case 6: return launch_w<B3, 6>(a, nsub, B, st);
-        case 7: return launch_w<B3, 7>(a, nsub, B, st);
-        case 8: return launch_w<B3, 8>(a, nsub, B, st);
+        case 2: return launch_w<B3, 2>(a, nsub, B, coils, st);
+        case 3: return launch_w<B3, 3>(a, nsub, B, coils, st);
+        case 4: return launch_w<B3, 4>(a, nsub, B, coils, st);
+        case 5: return launch_w<B3, 5>(a, nsub, B, coils, st);
+        case 6: return launch_w<B3, 6>(a, nsub, B, coils, st);
+        case 7: return launch_w<B3, 7>(a, nsub, B, coils, st);
+        case 8: return launch_w<B3, 8>(a, nsub, B, coils, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -61,12 +61,13 @@ class Tuning(ctypes.Structure):
         ("fft_lines", ctypes.c_int32),
         ("fft_cols", ctypes.c_int32),
         ("interp_threads", ctypes.c_int32),
+        ("spread_coils", ctypes.c_int32),
     ]
 
     @staticmethod
     def of(d):
         """From a dict {spread_bins: (8, 4, 8), spread_chunk: 512, fft_engine: 0, fft_lines: 0, fft_cols: 0,
-        interp_threads: 0}; missing keys take those defaults."""
+        interp_threads: 0, spread_coils: 0}; missing keys take those defaults."""
         t = Tuning()
         t.spread_bins = (ctypes.c_int32 * 3)(*[int(v) for v in d.get("spread_bins", (8, 4, 8))])
         t.spread_chunk = int(d.get("spread_chunk", 512))
@@ -74,12 +75,13 @@ class Tuning(ctypes.Structure):
         t.fft_lines = int(d.get("fft_lines", 0))
         t.fft_cols = int(d.get("fft_cols", 0))
         t.interp_threads = int(d.get("interp_threads", 0))
+        t.spread_coils = int(d.get("spread_coils", 0))
         return t
 
     def as_dict(self):
         return {"spread_bins": tuple(int(v) for v in self.spread_bins), "spread_chunk": int(self.spread_chunk),
                 "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines), "fft_cols": int(self.fft_cols),
-                "interp_threads": int(self.interp_threads)}
+                "interp_threads": int(self.interp_threads), "spread_coils": int(self.spread_coils)}
 
 
 class Work(ctypes.Structure):

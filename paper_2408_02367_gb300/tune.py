@@ -11,7 +11,9 @@ the operator computes, only how fast it runs on a given trajectory and volume:
 - FFT engine: the two-pass register FFTs or the Stockham kernels;
 - FFT lines per CTA of the fused axis-3 prologue and epilogue (16, 8 or 4);
 - FFT columns per CTA of the strided axis-1/axis-2 passes (16, 32 or 8);
-- threads per CTA of the persistent interpolation kernel (1024 or 256).
+- threads per CTA of the persistent interpolation kernel (1024 or 256);
+- coils per spread warp (two coils share the staging of each incidence where
+  their register columns fit, or one).
 
 `autotune` builds a plan for every candidate on the caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
@@ -33,14 +35,14 @@ import torch
 from . import op as _op
 
 DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 0,
-           "interp_threads": 0}
+           "interp_threads": 0, "spread_coils": 0}
 
 
 def candidates(full: bool = False):
     """The tunings tried: both bin depths x three chunk lengths with the two-pass
     FFTs, both bin depths with 8 and 4 FFT lines per CTA, 32 and 8 strided FFT
-    columns per CTA, 256-thread interpolation CTAs, and the Stockham engine on
-    the default spread; `full` adds more chunks."""
+    columns per CTA, 256-thread interpolation CTAs, one coil per spread warp,
+    and the Stockham engine on the default spread; `full` adds more chunks."""
     chunks = (128, 256, 512, 1024, 2048) if full else (256, 512, 1024)
     out = []
     for bins in ((8, 4, 8), (8, 4, 4)):
@@ -52,6 +54,7 @@ def candidates(full: bool = False):
     for cols in (32, 8):
         out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": cols})
     out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256})
+    out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "spread_coils": 1})
     out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
     return out
 

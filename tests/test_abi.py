@@ -106,6 +106,8 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({"interp_threads": 512})                                 # 0, 256 or 1024 only
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"spread_coils": 3})                                     # 0, 1 or 2 only
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})                                                       # valid tuning, no descriptor
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     assert lib.sdp_plan_tuning(None, ctypes.byref(t)) == 1

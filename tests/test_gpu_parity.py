@@ -163,16 +163,19 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 8},
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
     {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "interp_threads": 1024},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 64, "fft_engine": 0, "spread_coils": 1},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 64, "fft_engine": 0, "spread_coils": 2},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, short spread
-    chunks (many multi-chunk bins) and the Stockham FFT engine, forward and adjoint."""
+    chunks (many multi-chunk bins), one or two coils per spread warp (three coils:
+    a pair and an odd tail) and the Stockham FFT engine, forward and adjoint."""
     from paper_2408_02367_gb300 import op
-    c = make_case((20, 18, 16), 4, 1.25, 3, 3, 10, 1, 600, [2, 0])
+    c = make_case((20, 18, 16), 4, 1.25, 3, 3, 10, 1, 600, [2, 0, 1])
     geo = O.Geometry(c["n"], 4, 1.25)
-    A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2, tuning=tuning)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3, tuning=tuning)
     assert A.tuning["spread_bins"] == tuple(tuning["spread_bins"]) and A.tuning["spread_chunk"] == tuning["spread_chunk"]
-    assert A.tuning["interp_threads"] == (tuning.get("interp_threads") or 1024)     # W = 4: 1024 by default
+    assert A.tuning["interp_threads"] == (tuning.get("interp_threads") or 256)      # 256 by default
     y = A.forward(t(c["x"]), t(c["coils"])).cpu().numpy()
     assert_close(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
                  f"{tuning} forward")
