@@ -437,6 +437,12 @@ WHOLE_BRAIN_CANDIDATES = [
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
      "spread_coils": 1},
     {"spread_bins": (8, 4, 4), "spread_chunk": 1024, "fft_engine": 0, "fft_lines": 4, "interp_threads": 256},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
+     "interp_coils": 2},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
+     "interp_coils": 2, "interp_run": 2},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
+     "interp_coils": 2},
 ]
 
 
@@ -690,7 +696,9 @@ def run_native(args):
     x_hat = synth.ellipsoid_phantom(w.n, w.K, seed=1)
     # kernel shapes: the framework's autotuner on this trajectory and volume
     tuning, tune_table = None, None
-    if not args.no_tune:
+    if args.tuning:
+        tuning = json.loads(args.tuning)          # given kernel shapes (reproducible profiling runs)
+    elif not args.no_tune:
         from paper_2408_02367_gb300 import tune
         tuning, tune_table = tune.autotune(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=max(B, 1), B=B,
                                            reps=7, device=dev)
@@ -875,117 +883,119 @@ def run_native(args):
         mv_tuning = dict(scale["whole_brain"]["tuning"]) if not args.no_tune else None
         scale["multi_volume"] = multi_volume_rows(args, torch, op, dev, mv_tuning, flush, hbm)
 
-    # ---- rows built on the operator: DCF estimation, SVD-MRF initialiser, CG iteration ----
-    from paper_2408_02367_gb300 import recon
+    rows = {}
+    if not args.no_operator_rows:
+        # ---- rows built on the operator: DCF estimation, SVD-MRF initialiser, CG iteration ----
+        from paper_2408_02367_gb300 import recon
 
-    def event_ms(fn, reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        fn()
-        torch.cuda.synchronize()
-        a.record()
-        for _ in range(reps):
+        def event_ms(fn, reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
 
-    Ad = recon.dcf_operator(omega, w.n, w.width, w.oversamp, device=dev)
-    dcf_iters = 10
-    dcf_ms = event_ms(lambda: recon.dcf_pipe_menon(Ad, iters=dcf_iters), 2) / dcf_iters
-    dcf = recon.dcf_pipe_menon(Ad, iters=dcf_iters)
-    dcf = dcf / dcf.mean()
-    del Ad
-    init_ms = event_ms(lambda: recon.svd_mrf_init(A, y_meas, dcf), 2)
-    cg_iters = 3
-    cg_ms = event_ms(lambda: recon.cg_normal(A, y_meas, dcf, iters=cg_iters), 1) / (cg_iters + 1)
-    xtv = x.detach()
-    tv_grad_buf = torch.empty_like(xtv)
-    tv_val_buf = torch.empty((), dtype=torch.float32, device=dev)
+        Ad = recon.dcf_operator(omega, w.n, w.width, w.oversamp, device=dev)
+        dcf_iters = 10
+        dcf_ms = event_ms(lambda: recon.dcf_pipe_menon(Ad, iters=dcf_iters), 2) / dcf_iters
+        dcf = recon.dcf_pipe_menon(Ad, iters=dcf_iters)
+        dcf = dcf / dcf.mean()
+        del Ad
+        init_ms = event_ms(lambda: recon.svd_mrf_init(A, y_meas, dcf), 2)
+        cg_iters = 3
+        cg_ms = event_ms(lambda: recon.cg_normal(A, y_meas, dcf, iters=cg_iters), 1) / (cg_iters + 1)
+        xtv = x.detach()
+        tv_grad_buf = torch.empty_like(xtv)
+        tv_val_buf = torch.empty((), dtype=torch.float32, device=dev)
 
-    def kernel_ms(fn, reps):
-        # device time of the library call alone (its own events), L2 flushed before each call
-        fn()
-        A.profile_read()
-        A.profile(True)
-        for i in range(reps):
-            flush.fill_(float(i))
+        def kernel_ms(fn, reps):
+            # device time of the library call alone (its own events), L2 flushed before each call
             fn()
-        A.profile(False)
-        torch.cuda.synchronize()
-        ms, n = A.profile_read()["tv"]
-        return ms / n
+            A.profile_read()
+            A.profile(True)
+            for i in range(reps):
+                flush.fill_(float(i))
+                fn()
+            A.profile(False)
+            torch.cuda.synchronize()
+            ms, n = A.profile_read()["tv"]
+            return ms / n
 
-    tv_val_ms = kernel_ms(lambda: A.tv_value(xtv, 1e-7, 1e-6, out=tv_val_buf), 20)
-    tv_grad_ms = kernel_ms(lambda: A.tv_grad(xtv, 1e-7, 1e-6, out=tv_grad_buf), 20)
-    xb = 8.0 * xtv.numel()
+        tv_val_ms = kernel_ms(lambda: A.tv_value(xtv, 1e-7, 1e-6, out=tv_val_buf), 20)
+        tv_grad_ms = kernel_ms(lambda: A.tv_grad(xtv, 1e-7, 1e-6, out=tv_grad_buf), 20)
+        xb = 8.0 * xtv.numel()
 
-    # dictionary matching of the whole TSMI volume against a synthetic MRF dictionary
-    from paper_2408_02367_gb300 import dm as dm_mod
-    fp, params = synth.mrf_dictionary(480, 128, 96)
-    Dm, _ = synth.compress_dictionary(fp, w.K)
-    xd_np, _, _ = synth.dm_volume(Dm, w.nvox, noise=0.01, seed=7)
-    xd = torch.from_numpy(xd_np.reshape((w.K,) + tuple(w.n))).to(dev)
-    del xd_np
-    matcher = dm_mod.DictionaryMatcher(torch.from_numpy(Dm).to(dev), max_vox=w.nvox,
-                                       params=torch.from_numpy(params).to(dev))
-    dm_out = (torch.empty(tuple(w.n), dtype=torch.int32, device=dev),
-              torch.empty(tuple(w.n), dtype=torch.complex64, device=dev),
-              torch.empty(tuple(w.n) + (2,), dtype=torch.float32, device=dev))
+        # dictionary matching of the whole TSMI volume against a synthetic MRF dictionary
+        from paper_2408_02367_gb300 import dm as dm_mod
+        fp, params = synth.mrf_dictionary(480, 128, 96)
+        Dm, _ = synth.compress_dictionary(fp, w.K)
+        xd_np, _, _ = synth.dm_volume(Dm, w.nvox, noise=0.01, seed=7)
+        xd = torch.from_numpy(xd_np.reshape((w.K,) + tuple(w.n))).to(dev)
+        del xd_np
+        matcher = dm_mod.DictionaryMatcher(torch.from_numpy(Dm).to(dev), max_vox=w.nvox,
+                                           params=torch.from_numpy(params).to(dev))
+        dm_out = (torch.empty(tuple(w.n), dtype=torch.int32, device=dev),
+                  torch.empty(tuple(w.n), dtype=torch.complex64, device=dev),
+                  torch.empty(tuple(w.n) + (2,), dtype=torch.float32, device=dev))
 
-    def dm_call():
-        matcher.match(xd, out=dm_out, qmap=True)
+        def dm_call():
+            matcher.match(xd, out=dm_out, qmap=True)
 
-    dm_call()
-    torch.cuda.synchronize()
-    dm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-    for i, (a_ev, b_ev) in enumerate(dm_ev):
-        flush.fill_(float(i))
-        a_ev.record()
         dm_call()
-        b_ev.record()
-    torch.cuda.synchronize()
-    dm_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in dm_ev)[len(dm_ev) // 2]
-    dm_info = matcher.info()
-    dm_status = matcher.status()
-    dm_tflops = dm_info["flops_per_voxel"] * w.nvox / (dm_ms * 1e-3) / 1e12
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
-    del matcher, xd, dm_out
+        torch.cuda.synchronize()
+        dm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for i, (a_ev, b_ev) in enumerate(dm_ev):
+            flush.fill_(float(i))
+            a_ev.record()
+            dm_call()
+            b_ev.record()
+        torch.cuda.synchronize()
+        dm_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in dm_ev)[len(dm_ev) // 2]
+        dm_info = matcher.info()
+        dm_status = matcher.status()
+        dm_tflops = dm_info["flops_per_voxel"] * w.nvox / (dm_ms * 1e-3) / 1e12
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
+        del matcher, xd, dm_out
 
-    # the full stochastic DIP iteration of Algorithm 1 with the 4-level 3D U-Net generator and Adam
-    from paper_2408_02367_gb300 import dip
-    torch.backends.cudnn.benchmark = True
-    torch.manual_seed(0)
-    net = dip.UNet3D(2 * w.K, 2 * w.K).to(dev)
-    z = torch.rand((1, 2 * w.K) + tuple(w.n), generator=torch.Generator().manual_seed(1)).mul_(0.1).to(dev)
-    runner = dip.DipRunner(A, y_meas, net, z, B=B, lr=1e-3)
-    for _ in range(3):
-        runner.step()
-    torch.cuda.synchronize()
-    un_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-    for a_ev, b_ev in un_ev:
-        a_ev.record()
-        runner.step()
-        b_ev.record()
-    torch.cuda.synchronize()
-    unet_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in un_ev)[len(un_ev) // 2]
-    del runner, net, z
+        # the full stochastic DIP iteration of Algorithm 1 with the 4-level 3D U-Net generator and Adam
+        from paper_2408_02367_gb300 import dip
+        torch.backends.cudnn.benchmark = True
+        torch.manual_seed(0)
+        net = dip.UNet3D(2 * w.K, 2 * w.K).to(dev)
+        z = torch.rand((1, 2 * w.K) + tuple(w.n), generator=torch.Generator().manual_seed(1)).mul_(0.1).to(dev)
+        runner = dip.DipRunner(A, y_meas, net, z, B=B, lr=1e-3)
+        for _ in range(3):
+            runner.step()
+        torch.cuda.synchronize()
+        un_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a_ev, b_ev in un_ev:
+            a_ev.record()
+            runner.step()
+            b_ev.record()
+        torch.cuda.synchronize()
+        unet_ms = sorted(a_ev.elapsed_time(b_ev) for a_ev, b_ev in un_ev)[len(un_ev) // 2]
+        del runner, net, z
 
-    rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
-            "tv_value_ms": tv_val_ms, "tv_value_gbs": xb / (tv_val_ms * 1e-3) / 1e9,
-            "tv_grad_ms": tv_grad_ms, "tv_grad_gbs": 2 * xb / (tv_grad_ms * 1e-3) / 1e9,
-            "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
-            "dip_unet_step_ms": unet_ms,
-            "dip_unet_note": "G(z) by a 4-level 3D U-Net (32..256 channels, cuDNN, TF32 convolutions allowed), "
-                             "DC loss of a coil minibatch through the library, backward, Adam; median of 5",
-            "dm_ms": dm_ms, "dm_atoms": int(Dm.shape[0]), "dm_voxels": int(w.nvox),
-            "dm_gpairs_per_s": w.nvox * Dm.shape[0] / (dm_ms * 1e-3) / 1e9,
-            "dm_tensor_tflops": dm_tflops, "dm_tensor_frac_of_measured_bf16": dm_tflops / bf16_peak,
-            "dm_status": dm_status,
-            "note": "all C coils per CG iteration in minibatches of B; DCF by Pipe-Menon on the interpolator; "
-                    "TV kernels timed alone by the library's stage events, L2 flushed before each call; "
-                    "dictionary matching: one match of all voxels (prep + tcgen05 score GEMM + refine), "
-                    "median of 5, L2 flushed before each, fp16 tensor flops counted with padding to K=16"}
+        rows = {"dcf_pipe_menon_ms_per_iter": dcf_ms, "svd_mrf_init_ms": init_ms, "cg_ms_per_iter": cg_ms,
+                "tv_value_ms": tv_val_ms, "tv_value_gbs": xb / (tv_val_ms * 1e-3) / 1e9,
+                "tv_grad_ms": tv_grad_ms, "tv_grad_gbs": 2 * xb / (tv_grad_ms * 1e-3) / 1e9,
+                "cg_nu_samples_per_s": w.C * w.J / (cg_ms * 1e-3),
+                "dip_unet_step_ms": unet_ms,
+                "dip_unet_note": "G(z) by a 4-level 3D U-Net (32..256 channels, cuDNN, TF32 convolutions allowed), "
+                                 "DC loss of a coil minibatch through the library, backward, Adam; median of 5",
+                "dm_ms": dm_ms, "dm_atoms": int(Dm.shape[0]), "dm_voxels": int(w.nvox),
+                "dm_gpairs_per_s": w.nvox * Dm.shape[0] / (dm_ms * 1e-3) / 1e9,
+                "dm_tensor_tflops": dm_tflops, "dm_tensor_frac_of_measured_bf16": dm_tflops / bf16_peak,
+                "dm_status": dm_status,
+                "note": "all C coils per CG iteration in minibatches of B; DCF by Pipe-Menon on the interpolator; "
+                        "TV kernels timed alone by the library's stage events, L2 flushed before each call; "
+                        "dictionary matching: one match of all voxels (prep + tcgen05 score GEMM + refine), "
+                        "median of 5, L2 flushed before each, fp16 tensor flops counted with padding to K=16"}
 
     # ---- roofline of the dominant kernel ----
     sb = stage_bytes(w, B, M, info["ninc"])
@@ -1057,10 +1067,13 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default kernel shapes instead of the autotuner's")
+    ap.add_argument("--tuning", default="", help="kernel shapes as JSON (sdp_tuning fields) instead of the autotuner's")
     ap.add_argument("--cpu-whole-brain", action="store_true",
                     help="also time one coil x all K of the 200x200x160 workload on the CPU oracle")
     ap.add_argument("--no-scale-rows", action="store_true",
                     help="skip the whole-brain minibatch rows and the six-volume batch")
+    ap.add_argument("--no-operator-rows", action="store_true",
+                    help="skip the rows built on the operator (DCF, SVD-MRF, CG, TV, dictionary matching, U-Net step)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed DIP steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)

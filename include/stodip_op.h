@@ -151,6 +151,15 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 with at most 5 channels per group, else one), 1 or 2 (2 falls
  *                 back to one where it does not fit).  Two coils share one
  *                 staging of each incidence's positions, weights and coverage.
+ *   interp_run    consecutive bin-sorted samples one interpolation warp takes
+ *                 before it jumps ahead by the whole grid of warps: 0 (default:
+ *                 1), 1, 2, 4 or 8.  Longer runs let a warp's next sample find
+ *                 its window rows in the SM's L1.
+ *   interp_coils  coils of the minibatch per sweep of the interpolation over
+ *                 the samples: 0 (default: all of them, each sample's window
+ *                 set up once) or 1 .. 64 (e.g. 2: the samples are swept B / 2
+ *                 times, each sweep gathering from two coils' grids only, which
+ *                 keeps a large minibatch's working set within L2 and the TLB).
  */
 typedef struct {
     int32_t spread_bins[3];
@@ -160,6 +169,8 @@ typedef struct {
     int32_t fft_cols;
     int32_t interp_threads;
     int32_t spread_coils;
+    int32_t interp_run;
+    int32_t interp_coils;
 } sdp_tuning;
 
 /*

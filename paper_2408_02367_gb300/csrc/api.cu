@@ -46,6 +46,8 @@ struct sdp_plan_s {
     int spread_chunk = 0;
     int interp_threads = 0;   // resolved CTA size of the interpolation kernel
     int spread_coils = 0;     // coils per spread warp: 0 = two where they fit, 1 = one
+    int interp_run = 1;       // consecutive samples per interpolation warp run
+    int interp_coils = 0;     // coils per interpolation sweep over the samples: 0 = all
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -214,6 +216,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     if (ithreads == 1024 && W > 4) return SDP_ERR_UNSUPPORTED;
     p->interp_threads = ithreads ? ithreads : 256;
     p->spread_coils = tn ? tn->spread_coils : 0;
+    p->interp_run = (tn && tn->interp_run) ? tn->interp_run : 1;
+    p->interp_coils = tn ? tn->interp_coils : 0;
 
     // ---- host tables ----
     std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
@@ -500,7 +504,7 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
         return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3 * nk, B, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->interp_threads, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk,
+        return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk,
                              static_cast<float2*>(y), accumulate, st);
     }));
     return SDP_OK;
@@ -573,7 +577,7 @@ bool fused_eligible(const sdp_work* items, int n) {
     for (int i = 0; i < n; ++i) {
         const sdp_plan_s* p = items[i].plan;
         if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[2] != p0->bs[2] ||
-            p->interp_threads != p0->interp_threads)
+            p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils)
             return false;
         if (p->geo.K > 8 || p->geo.K > 32 / p->geo.W || !mv_width_supported(p->geo.W)) return false;
         for (int a = 0; a < 3; ++a)
@@ -655,6 +659,7 @@ int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vect
         sa.group = 0;
         it.nsub = p->nsub;
         it.spread_pairs = (spread_pairs_fit(p->bs[2], g.K) && p->spread_coils != 1 && w.B >= 2) ? 1 : 0;
+        it.interp_coils = p->interp_coils > 0 && p->interp_coils < w.B ? p->interp_coils : w.B;
     }
     // units of each stage
     auto units = [&](auto count) {
@@ -820,7 +825,10 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
             (tn->fft_lines != 0 && tn->fft_lines != 8 && tn->fft_lines != 4) ||
             (tn->fft_cols != 0 && tn->fft_cols != 32 && tn->fft_cols != 8) ||
             (tn->interp_threads != 0 && tn->interp_threads != 256 && tn->interp_threads != 1024) ||
-            tn->spread_coils < 0 || tn->spread_coils > 2)
+            tn->spread_coils < 0 || tn->spread_coils > 2 ||
+            (tn->interp_run != 0 && tn->interp_run != 1 && tn->interp_run != 2 && tn->interp_run != 4 &&
+             tn->interp_run != 8) ||
+            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch)
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -918,7 +926,7 @@ int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* st
                              p->counters, p->nbins, p->spread_coils, st);
     }));
     return run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->interp_threads, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K,
+        return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K,
                              static_cast<float2*>(out), 0, st);
     });
 }
@@ -974,6 +982,8 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->fft_cols = p->ax[0].cols;
     out->interp_threads = p->interp_threads;
     out->spread_coils = p->spread_coils;
+    out->interp_run = p->interp_run;
+    out->interp_coils = p->interp_coils;
     return SDP_OK;
 }
 

@@ -40,6 +40,7 @@ struct MvItem {
     SpreadArgs sa;
     int nsub;
     int spread_pairs;         // 1: one spread warp holds two coils
+    int interp_coils;         // coils per interpolation sweep over the samples (B: all at once)
 };
 
 struct MvArgs {

@@ -33,22 +33,27 @@ __device__ __forceinline__ void mv_interp_item(const MvArgs& a, const MvUnits& u
     const long long gs0 = s0 <= first ? first : first + (s0 - first + step - 1) / step * step;
     if (gs0 >= s1) return;
     const MvItem& it = a.it[I];
-    long long s = gs0 - s0;
     const long long J = s1 - s0;
-    float4 pn = __ldg(it.pts + s);
-    int tn = __ldg(it.tframe + s);
-    float wn = lane < 3 * W ? __ldg(it.wts + s * (3 * W) + lane) : 0.f;
-    for (; s < J; s += step) {
-        const float4 p = pn;
-        const int t = tn;
-        const float wv = wn;
-        const long long sn = s + step;
-        if (sn < J) {
-            pn = __ldg(it.pts + sn);
-            tn = __ldg(it.tframe + sn);
-            wn = lane < 3 * W ? __ldg(it.wts + sn * (3 * W) + lane) : 0.f;
+    const long long Gk = (long long)it.g.M[0] * it.g.M[1] * it.g.M[2] * it.g.K;
+    for (int b0 = 0; b0 < it.B; b0 += it.interp_coils) {     // one sweep per block of coils
+        const int nb = min(it.interp_coils, it.B - b0);
+        long long s = gs0 - s0;
+        float4 pn = __ldg(it.pts + s);
+        int tn = __ldg(it.tframe + s);
+        float wn = lane < 3 * W ? __ldg(it.wts + s * (3 * W) + lane) : 0.f;
+        for (; s < J; s += step) {
+            const float4 p = pn;
+            const int t = tn;
+            const float wv = wn;
+            const long long sn = s + step;
+            if (sn < J) {
+                pn = __ldg(it.pts + sn);
+                tn = __ldg(it.tframe + sn);
+                wn = lane < 3 * W ? __ldg(it.wts + sn * (3 * W) + lane) : 0.f;
+            }
+            interp_rows_sample<W>(it.g, rl, it.V, it.bufA + b0 * Gk, nb, 0, it.g.K, it.y + b0 * J, 0, p, t, wv,
+                                  lane);
         }
-        interp_rows_sample<W>(it.g, rl, it.V, it.bufA, it.B, 0, it.g.K, it.y, 0, p, t, wv, lane);
     }
 }
 

@@ -75,31 +75,43 @@ __global__ void __launch_bounds__(NT) interp_rows_kernel(Geo g, const float4* __
                                                               const float2* __restrict__ V,
                                                               const float2* __restrict__ grids, int B, int k0,
                                                               int nk, int c0, int cg, float2* __restrict__ y,
-                                                              int accumulate) {
+                                                              int accumulate, int run, int cblock) {
     const int lane = threadIdx.x & 31;
     const long long J = g.J;
     const long long first = ((long long)blockIdx.x * NT + threadIdx.x) >> 5;
     const long long step = ((long long)gridDim.x * NT) >> 5;
     const RowLane rl = row_lane<W>(lane, c0, cg);
+    const long long Gk = (long long)g.M[0] * g.M[1] * g.M[2] * nk;
+    // the samples are swept once per block of cblock coils (all B coils when cblock = 0):
+    // a sweep's gathers then touch only that block's grids
+    const int cb = cblock > 0 && cblock < B ? cblock : B;
+    for (int b0 = 0; b0 < B; b0 += cb) {
+    const int nb = min(cb, B - b0);
     float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
     int tn = 0;
     float wn = 0.f;
-    if (first < J) {
-        pn = __ldg(pts + first);
-        tn = __ldg(tframe + first);
-        wn = lane < 3 * W ? __ldg(wts + first * (3 * W) + lane) : 0.f;
+    long long s = first * run;    // warp w takes the runs w, w + step, ... of `run` consecutive samples
+    int r = 0;
+    if (s < J) {
+        pn = __ldg(pts + s);
+        tn = __ldg(tframe + s);
+        wn = lane < 3 * W ? __ldg(wts + s * (3 * W) + lane) : 0.f;
     }
-    for (long long s = first; s < J; s += step) {
+    while (s < J) {
         const float4 p = pn;
         const int t = tn;
         const float wv = wn;
-        const long long sn = s + step;
+        const bool in_run = r + 1 < run;
+        const long long sn = in_run ? s + 1 : s - r + step * run;
+        r = in_run ? r + 1 : 0;
         if (sn < J) {
             pn = __ldg(pts + sn);
             tn = __ldg(tframe + sn);
             wn = lane < 3 * W ? __ldg(wts + sn * (3 * W) + lane) : 0.f;
         }
-        interp_rows_sample<W>(g, rl, V, grids, B, k0, nk, y, accumulate, p, t, wv, lane);
+        interp_rows_sample<W>(g, rl, V, grids + b0 * Gk, nb, k0, nk, y + b0 * J, accumulate, p, t, wv, lane);
+        s = sn;
+    }
     }
 }
 
@@ -174,7 +186,8 @@ __global__ void __launch_bounds__(kThreads) interp_taps_kernel(Geo g, const floa
 
 template <int W, int NT>
 cudaError_t launch_rows(const Geo& g, const float4* pts, const int* tframe, const float* wts, const float2* V,
-                        const float2* grids, int B, int k0, int nk, float2* y, int accumulate, cudaStream_t st) {
+                        const float2* grids, int B, int k0, int nk, float2* y, int accumulate, int run,
+                        int cblock, cudaStream_t st) {
     // persistent grid: the CTAs that are resident at once (or fewer for a short trajectory)
     static std::atomic<int> resident{0};
     int per_sm = resident.load(std::memory_order_relaxed);
@@ -190,13 +203,13 @@ cudaError_t launch_rows(const Geo& g, const float4* pts, const int* tframe, cons
                                                   cudaSuccess || nsm < 1)
         return cudaErrorInvalidDevice;
     const long long nres = (long long)nsm * per_sm;
-    const long long nneed = ((long long)g.J + NT / 32 - 1) / (NT / 32);
+    const long long nneed = ((long long)g.J + (long long)run * (NT / 32) - 1) / ((long long)run * (NT / 32));
     const unsigned nrow = (unsigned)(nneed < nres ? nneed : nres);
     constexpr int kGroup = 32 / W;   // channels per launch
     for (int c0 = 0; c0 < nk; c0 += kGroup) {
         const int cg = nk - c0 < kGroup ? nk - c0 : kGroup;
         interp_rows_kernel<W, NT><<<nrow, NT, 0, st>>>(g, pts, tframe, wts, V, grids, B, k0, nk, c0, cg, y,
-                                                      accumulate || c0 > 0);
+                                                      accumulate || c0 > 0, run, cblock);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (c0 > 0) note_launches(1);   // the stage counts its first launch
@@ -205,7 +218,8 @@ cudaError_t launch_rows(const Geo& g, const float4* pts, const int* tframe, cons
 }
 
 template <int W>
-cudaError_t launch_w(const Geo& g, int threads, const float4* pts, const int* tframe, const float* wts,
+cudaError_t launch_w(const Geo& g, int threads, int run, int cblock, const float4* pts, const int* tframe,
+                     const float* wts,
                      const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                      cudaStream_t st) {
     if (nk == 1) {
@@ -217,8 +231,9 @@ cudaError_t launch_w(const Geo& g, int threads, const float4* pts, const int* tf
         return cudaGetLastError();
     }
     if (W <= 4 && threads == 1024)
-        return launch_rows<W, (W <= 4 ? 1024 : 256)>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-    return launch_rows<W, 256>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        return launch_rows<W, (W <= 4 ? 1024 : 256)>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, run,
+                                                     cblock, st);
+    return launch_rows<W, 256>(g, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, run, cblock, st);
 }
 
 }  // namespace
@@ -231,17 +246,19 @@ cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(const Geo& g, int threads, const float4* pts, const int* tframe, const float* wts,
+cudaError_t launch_interp(const Geo& g, int threads, int run, int cblock, const float4* pts, const int* tframe,
+                          const float* wts,
                           const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                           cudaStream_t st) {
+    if (run < 1) run = 1;
     switch (g.W) {
-        case 2: return launch_w<2>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 3: return launch_w<3>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 4: return launch_w<4>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 5: return launch_w<5>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 6: return launch_w<6>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 7: return launch_w<7>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
-        case 8: return launch_w<8>(g, threads, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 2: return launch_w<2>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 3: return launch_w<3>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 4: return launch_w<4>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 5: return launch_w<5>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 6: return launch_w<6>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 7: return launch_w<7>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
+        case 8: return launch_w<8>(g, threads, run, cblock, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -111,7 +111,8 @@ cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const floa
 // Kaiser-Bessel weights of every (sorted) sample: wts[s][d][a] = phi(g_d - (m0_d + a)),
 // m0_d = ceil(g_d - W/2) in float32; computed once per plan.
 cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaStream_t st);
-cudaError_t launch_interp(const Geo& g, int threads, const float4* pts, const int* tframe, const float* wts,
+cudaError_t launch_interp(const Geo& g, int threads, int run, int cblock, const float4* pts, const int* tframe,
+                          const float* wts,
                           const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                           cudaStream_t st);
 cudaError_t launch_spread(const Geo& g, const int bs[3], const int nb[3], const SubProb* subs, int nsub,

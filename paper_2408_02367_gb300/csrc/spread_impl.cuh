@@ -107,18 +107,21 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
     constexpr int BP = B1 * B2 * B3;
     constexpr int NW = 3 * W;
     constexpr int NP = B1 + B2;               // staged axis-1 and axis-2 weights per incidence
-    // staging of 32 incidences, reused for the bin's store once they are summed; the
-    // channel coefficients of an incidence sit at an even stride NKP so that they, like
-    // the B3 (w3, w3) pairs, are read 16 bytes at a time.  With NC = 2 the warp spreads
-    // two coils of the minibatch: the positions, weights and coverage of an incidence are
-    // staged once and serve both, only the coefficients conj(V[t, k]) r_b are per coil.
-    constexpr int NKP = (NK + 1) & ~1;
-    constexpr int kStage = 32 * B3 * 8 + NC * 32 * NKP * 8 + 32 * NP * 4 + 32 * 4;
+    // staging of 32 incidences, reused for the bin's store once they are summed.  Every
+    // lane reads each incidence's record (a broadcast), and a 16-byte shared load costs
+    // two L1 wavefronts, so the records are packed: the B3 axis-3 weights as plain floats
+    // (the (w3, w3) pairs are formed in registers), and the coefficients conj(V[t, k]) r_b
+    // of all NC coils of the warp (NC = 2: the positions, weights and coverage of an
+    // incidence are staged once and serve both coils) in one run of NCK values, padded
+    // to an even count so that it is read 16 bytes at a time.
+    constexpr int NCK = NC * NK;
+    constexpr int NCKP = (NCK + 1) & ~1;
+    constexpr int kStage = 32 * B3 * 4 + 32 * NCKP * 8 + 32 * NP * 4 + 32 * 4;
     constexpr int kTr = 32 * ((B3 * NK / 2) | 1) * 16;
     __shared__ __align__(16) unsigned char sraw[kStage > kTr ? kStage : kTr];
-    float2* p3sm = reinterpret_cast<float2*>(sraw);  // [incidence][x3]: (w3, w3), 0 outside the window
-    float2* csm = p3sm + 32 * B3;                      // [coil][incidence][k]: conj(V[t, k]) r_b
-    float* psm = reinterpret_cast<float*>(csm + NC * 32 * NKP);  // [incidence][x1 (8) | x2 (4)], 0 outside
+    float* p3f = reinterpret_cast<float*>(sraw);       // [incidence][x3]: w3, 0 outside the window
+    float2* csm = reinterpret_cast<float2*>(p3f + 32 * B3);   // [incidence][coil][k]: conj(V[t, k]) r_b
+    float* psm = reinterpret_cast<float*>(csm + 32 * NCKP);   // [incidence][x1 (8) | x2 (4)], 0 outside
     unsigned* msm = reinterpret_cast<unsigned*>(psm + 32 * NP);   // axis-3 positions covered (bit x3)
     float4* tr = reinterpret_cast<float4*>(sraw);
     const Geo& g = a.g;
@@ -183,6 +186,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
                 pw[B1 + x] = v;
             }
             unsigned mask = 0;
+            float w3v[B3];
 #pragma unroll
             for (int x = 0; x < B3; ++x) {
                 int aa = lo3 + x - m03;
@@ -191,14 +195,18 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
                 float v = 0.f;
 #pragma unroll
                 for (int q = 0; q < W; ++q) v = aa == q ? wl[2 * W + q] : v;
-                p3sm[lane * B3 + x] = make_float2(v, v);
+                w3v[x] = v;
                 mask |= ((unsigned)aa < (unsigned)W ? 1u : 0u) << x;
             }
+#pragma unroll
+            for (int x = 0; x < B3; x += 4)
+                *reinterpret_cast<float4*>(p3f + lane * B3 + x) = make_float4(w3v[x], w3v[x + 1], w3v[x + 2], w3v[x + 3]);
             msm[lane] = mask;
             const float2* Vt = a.V + (long long)t * g.K + kv;
             float2 vq[NK];
 #pragma unroll
             for (int q = 0; q < NK; ++q) vq[q] = __ldg(Vt + q);
+            float2 cv[NCKP];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 float2 r = make_float2(0.f, 0.f);   // a missing second coil spreads zeros and is not stored
@@ -209,9 +217,12 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
                 }
 #pragma unroll
                 for (int q = 0; q < NK; ++q)
-                    csm[(c * 32 + lane) * NKP + q] =
-                        make_float2(vq[q].x * r.x + vq[q].y * r.y, vq[q].x * r.y - vq[q].y * r.x);
+                    cv[c * NK + q] = make_float2(vq[q].x * r.x + vq[q].y * r.y, vq[q].x * r.y - vq[q].y * r.x);
             }
+            if (NCKP > NCK) cv[NCKP - 1] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < NCKP; q += 2)
+                *reinterpret_cast<float4*>(csm + lane * NCKP + q) = make_float4(cv[q].x, cv[q].y, cv[q + 1].x, cv[q + 1].y);
         }
         __syncwarp();
         for (int i = 0; i < n; ++i) {
@@ -220,23 +231,22 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
             const float w12 = pw[x1] * pw[B1 + x2];
             unsigned long long w12p;
             asm("mov.b64 %0, {%1, %1};" : "=l"(w12p) : "f"(w12));
-            const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(p3sm + i * B3);
-            unsigned long long cc[NC][NK], wp3[B3];
+            const float4* wp = reinterpret_cast<const float4*>(p3f + i * B3);
+            const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(csm + i * NCKP);
+            unsigned long long cf[NCKP], wp3[B3];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(csm + (c * 32 + i) * NKP);
-#pragma unroll
-                for (int q = 0; q < NKP / 2; ++q) {
-                    const ulonglong2 v = cp[q];
-                    cc[c][2 * q] = v.x;
-                    if (2 * q + 1 < NK) cc[c][2 * q + 1] = v.y;
-                }
+            for (int q = 0; q < NCKP / 2; ++q) {
+                const ulonglong2 v = cp[q];
+                cf[2 * q] = v.x;
+                cf[2 * q + 1] = v.y;
             }
 #pragma unroll
-            for (int x3 = 0; x3 < B3 / 2; ++x3) {
-                const ulonglong2 v = wp[x3];
-                wp3[2 * x3] = v.x;
-                wp3[2 * x3 + 1] = v.y;
+            for (int x3 = 0; x3 < B3 / 4; ++x3) {
+                const float4 v = wp[x3];
+                asm("mov.b64 %0, {%1, %1};" : "=l"(wp3[4 * x3]) : "f"(v.x));
+                asm("mov.b64 %0, {%1, %1};" : "=l"(wp3[4 * x3 + 1]) : "f"(v.y));
+                asm("mov.b64 %0, {%1, %1};" : "=l"(wp3[4 * x3 + 2]) : "f"(v.z));
+                asm("mov.b64 %0, {%1, %1};" : "=l"(wp3[4 * x3 + 3]) : "f"(v.w));
             }
 #pragma unroll
             for (int x3 = 0; x3 < B3; ++x3) {
@@ -249,7 +259,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
                     for (int c = 0; c < NC; ++c)
 #pragma unroll
                         for (int q = 0; q < NK; ++q)
-                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[c][x3][q]) : "l"(w), "l"(cc[c][q]));
+                            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[c][x3][q]) : "l"(w), "l"(cf[c * NK + q]));
                 }
             }
         }

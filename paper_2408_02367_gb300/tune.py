@@ -13,7 +13,9 @@ the operator computes, only how fast it runs on a given trajectory and volume:
 - FFT columns per CTA of the strided axis-1/axis-2 passes (16, 32 or 8);
 - threads per CTA of the persistent interpolation kernel (1024 or 256);
 - coils per spread warp (two coils share the staging of each incidence where
-  their register columns fit, or one).
+  their register columns fit, or one);
+- consecutive samples per interpolation warp run, and coils per sweep of the
+  interpolation over the samples (all, or two at a time).
 
 `autotune` builds a plan for every candidate on the caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
@@ -35,7 +37,7 @@ import torch
 from . import op as _op
 
 DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 0,
-           "interp_threads": 0, "spread_coils": 0}
+           "interp_threads": 0, "spread_coils": 0, "interp_run": 0, "interp_coils": 0}
 
 
 def candidates(full: bool = False):
@@ -55,6 +57,9 @@ def candidates(full: bool = False):
         out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": cols})
     out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256})
     out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "spread_coils": 1})
+    for run in (1, 2):
+        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                    "interp_threads": 1024, "interp_run": run, "interp_coils": 2})
     out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
     return out
 

@@ -108,6 +108,10 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({"spread_coils": 3})                                     # 0, 1 or 2 only
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"interp_run": 3})                                       # 0, 1, 2, 4 or 8 only
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"interp_coils": -1})                                    # 0 .. 64
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({})                                                       # valid tuning, no descriptor
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     assert lib.sdp_plan_tuning(None, ctypes.byref(t)) == 1

@@ -165,6 +165,9 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "interp_threads": 1024},
     {"spread_bins": (8, 4, 4), "spread_chunk": 64, "fft_engine": 0, "spread_coils": 1},
     {"spread_bins": (8, 4, 4), "spread_chunk": 64, "fft_engine": 0, "spread_coils": 2},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "interp_threads": 1024, "interp_run": 2,
+     "interp_coils": 2},
+    {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "interp_run": 8, "interp_coils": 1},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, short spread
