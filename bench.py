@@ -443,6 +443,8 @@ WHOLE_BRAIN_CANDIDATES = [
      "interp_coils": 2, "interp_run": 2},
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
      "interp_coils": 2},
+    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
+     "fft_staged": 1},
 ]
 
 

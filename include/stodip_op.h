@@ -160,6 +160,11 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 set up once) or 1 .. 64 (e.g. 2: the samples are swept B / 2
  *                 times, each sweep gathering from two coils' grids only, which
  *                 keeps a large minibatch's working set within L2 and the TLB).
+ *   fft_staged    fused axis-3 kernels with their inputs staged by bulk copies
+ *                 (cp.async.bulk into double-buffered shared memory, persistent
+ *                 CTAs, whole image rows per unit): 0 (default: off) or 1 (on
+ *                 where supported: a two-pass length, even N3, 16-byte aligned
+ *                 x and S; elsewhere the direct-load kernels run).
  */
 typedef struct {
     int32_t spread_bins[3];
@@ -171,6 +176,7 @@ typedef struct {
     int32_t spread_coils;
     int32_t interp_run;
     int32_t interp_coils;
+    int32_t fft_staged;
 } sdp_tuning;
 
 /*

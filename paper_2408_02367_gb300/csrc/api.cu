@@ -210,6 +210,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
         p->ax[a].generic = tn ? tn->fft_engine : 0;
         p->ax[a].lines = tn ? tn->fft_lines : 0;
         p->ax[a].cols = tn ? tn->fft_cols : 0;
+        p->ax[a].staged = tn ? tn->fft_staged : 0;
     }
     // interpolation CTA size: the 1024-thread kernel is built for W <= 4 only
     const int ithreads = tn ? tn->interp_threads : 0;
@@ -828,7 +829,7 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
             tn->spread_coils < 0 || tn->spread_coils > 2 ||
             (tn->interp_run != 0 && tn->interp_run != 1 && tn->interp_run != 2 && tn->interp_run != 4 &&
              tn->interp_run != 8) ||
-            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch)
+            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch || tn->fft_staged < 0 || tn->fft_staged > 1)
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -984,6 +985,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->spread_coils = p->spread_coils;
     out->interp_run = p->interp_run;
     out->interp_coils = p->interp_coils;
+    out->fft_staged = p->ax[2].staged;
     return SDP_OK;
 }
 

@@ -398,8 +398,11 @@ cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int* status,
                                      cudaStream_t st) {
-    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic)
+    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic) {
+        if (ax.staged && fft2_prologue_staged_ok(g, ax, x, S, nk))
+            return launch_fft2_prologue_staged(g, ax, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, status, st);
         return launch_fft2_fwd_prologue(g, ax, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, status, st);
+    }
     const size_t sm = smem_fft_bytes(ax.L);
     const long long nlines = (long long)g.N[0] * g.N[1] * nk;
     const long long nblk = (nlines + NL - 1) / NL;

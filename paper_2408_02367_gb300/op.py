@@ -64,6 +64,7 @@ class Tuning(ctypes.Structure):
         ("spread_coils", ctypes.c_int32),
         ("interp_run", ctypes.c_int32),
         ("interp_coils", ctypes.c_int32),
+        ("fft_staged", ctypes.c_int32),
     ]
 
     @staticmethod
@@ -80,13 +81,15 @@ class Tuning(ctypes.Structure):
         t.spread_coils = int(d.get("spread_coils", 0))
         t.interp_run = int(d.get("interp_run", 0))
         t.interp_coils = int(d.get("interp_coils", 0))
+        t.fft_staged = int(d.get("fft_staged", 0))
         return t
 
     def as_dict(self):
         return {"spread_bins": tuple(int(v) for v in self.spread_bins), "spread_chunk": int(self.spread_chunk),
                 "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines), "fft_cols": int(self.fft_cols),
                 "interp_threads": int(self.interp_threads), "spread_coils": int(self.spread_coils),
-                "interp_run": int(self.interp_run), "interp_coils": int(self.interp_coils)}
+                "interp_run": int(self.interp_run), "interp_coils": int(self.interp_coils),
+                "fft_staged": int(self.fft_staged)}
 
 
 class Work(ctypes.Structure):

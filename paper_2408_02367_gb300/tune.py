@@ -15,7 +15,8 @@ the operator computes, only how fast it runs on a given trajectory and volume:
 - coils per spread warp (two coils share the staging of each incidence where
   their register columns fit, or one);
 - consecutive samples per interpolation warp run, and coils per sweep of the
-  interpolation over the samples (all, or two at a time).
+  interpolation over the samples (all, or two at a time);
+- the forward prologue with its inputs staged by bulk copies, or loaded directly.
 
 `autotune` builds a plan for every candidate on the caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
@@ -60,6 +61,9 @@ def candidates(full: bool = False):
     for run in (1, 2):
         out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
                     "interp_threads": 1024, "interp_run": run, "interp_coils": 2})
+    for threads, run in ((1024, 2), (256, 1)):
+        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                    "interp_threads": threads, "interp_run": run, "interp_coils": 2, "fft_staged": 1})
     out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
     return out
 

@@ -337,3 +337,36 @@ def test_autograd_gradient_matches_oracle_adjoint():
     assert_close(xg.grad.cpu().numpy(), g_ref, 1e-4, "autograd gradient vs oracle A^H(2r)")
     l_ref = O.dip_loss(fwd, c["x"].astype(np.complex128), y_meas)
     assert abs(loss.item() - l_ref) / l_ref < 1e-4
+
+
+@pytest.mark.parametrize("n,K,coils", [((8, 16, 128), 5, [1, 0]), ((24, 20, 64), 5, [0, 1, 1]),
+                                       ((6, 10, 160), 3, [1]), ((10, 12, 63), 5, [1, 0]),
+                                       ((12, 8, 200), 8, [0, 1])])
+def test_staged_prologue_equals_direct_prologue(n, K, coils):
+    """The fused prologue with bulk-copy staged inputs (fft_staged = 1) computes the same forward
+    operator as the direct-load kernel (the same operations per grid line; the compiler may fuse
+    a multiply-add differently, so agreement is to float32 rounding, not bits), on grid lengths
+    160, 80, 200, 250 and with an odd N3 (where the direct kernel runs)."""
+    from paper_2408_02367_gb300 import op
+    c = make_case(n, 4, 1.25, K, 2, 6, 1, 300, coils)
+    geo = O.Geometry(c["n"], 4, 1.25)
+    base = {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8}
+    A0 = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3, tuning=base)
+    A1 = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3,
+                          tuning=dict(base, fft_staged=1))
+    assert A1.tuning["fft_staged"] == 1
+    x, ci = t(c["x"]), t(c["coils"])
+    y0, y1 = A0.forward(x, ci), A1.forward(x, ci)
+    assert (torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)).item() < 1e-6
+    assert_close(y1.cpu().numpy(), O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"],
+                                                      c["coils"]), FP32_BOUND, f"staged prologue {n}")
+    # a channel subset (nk < K) and an out-of-range coil index (status, zeros)
+    ys = torch.zeros_like(y1)
+    A1.forward(x, ci, out=ys, k0=1, nk=K - 1, accumulate=True)
+    ys0 = torch.zeros_like(y0)
+    A0.forward(x, ci, out=ys0, k0=1, nk=K - 1, accumulate=True)
+    assert (torch.linalg.norm(ys - ys0) / torch.linalg.norm(ys0)).item() < 1e-6
+    assert A1.status() == 0
+    bad = torch.tensor([0, 9], dtype=torch.int32, device="cuda")
+    yb = A1.forward(x, bad)
+    assert A1.status() == 5 and torch.all(yb[1] == 0)
