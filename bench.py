@@ -430,21 +430,19 @@ def _plain_step(A, torch, x, y_meas, ci, K):
     return y_p, loss, g
 
 
+# whole-brain autotuning at B = 8 (each candidate builds a 16 GB plan): the spread's
+# bin shapes first, then the FFT / interpolation knobs on the fastest spread
 WHOLE_BRAIN_CANDIDATES = [
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024},
-    {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
-     "spread_coils": 1},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 1024, "fft_engine": 0, "fft_lines": 4, "interp_threads": 256},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
-     "interp_coils": 2},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
-     "interp_coils": 2, "interp_run": 2},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256,
-     "interp_coils": 2},
-    {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
-     "fft_staged": 1},
+    {"spread_bins": bins, "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024}
+    for bins in ((8, 4, 4), (4, 4, 4), (4, 4, 8), (8, 4, 8))
+] + [{"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024,
+      "spread_coils": 1}]
+WHOLE_BRAIN_REFINE = [
+    {"fft_lines": 8, "interp_threads": 256},
+    {"fft_lines": 8, "interp_threads": 1024, "interp_coils": 2},
+    {"fft_lines": 8, "interp_threads": 1024, "interp_coils": 2, "interp_run": 2},
+    {"fft_lines": 8, "interp_threads": 256, "interp_coils": 2},
+    {"fft_lines": 8, "interp_threads": 1024, "fft_staged": 1},
 ]
 
 
@@ -466,7 +464,8 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
         # kernel shapes for this workload, by the autotuner on its own trajectory at B = 8
         from paper_2408_02367_gb300 import tune
         tuning, tune_table = tune.autotune(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=Bmax, B=Bmax,
-                                           cands=WHOLE_BRAIN_CANDIDATES, reps=3, device=dev)
+                                           cands=WHOLE_BRAIN_CANDIDATES, refine=WHOLE_BRAIN_REFINE, reps=3,
+                                           device=dev)
     A, plan_s = _upload_plan(op, torch, w, omega, frame, V, S, Bplan, dev, tuning)
     del S
     info = A.info()

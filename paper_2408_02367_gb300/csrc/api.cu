@@ -252,8 +252,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
         for (int a = 0; a < 3; ++a) gc[(size_t)j * 3 + a] = grid_coord(om[a], p->M[a]);
     }
 
-    // ---- bins: 8 x 4 x 8 grid points (one warp of the spread, a lane per axis-3
-    // column of 8 points held in registers) ----
+    // ---- bins: B1 x 4 x B3 grid points, 8 x 4 x 8 unless tuned (one warp of the
+    // spread; lanes own the B1 x 4 axis-3 columns, held in registers) ----
     int bs[3] = {8, 4, 8};
     if (tn)
         for (int a = 0; a < 3; ++a) bs[a] = tn->spread_bins[a];
@@ -349,6 +349,33 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
                         const long long bin = ((long long)b1[x] * p->nb[1] + b2[y]) * p->nb[2] + b3[z];
                         inc[cur[bin]++] = (int)s;
                     }
+        }
+    }
+    // each bin's incidences in order of axis-3 class (stable in sample order): the class
+    // is o + W - 1 for the bin position o in [-(W-1), B3-1] of the window's first axis-3
+    // tap, the same integer the spread kernel derives from the staged coordinate, which
+    // runs each class with code for exactly the positions it covers.  Grids too short
+    // along axis 3 for a window to meet a bin in one piece keep sample order.
+    if (p->M[2] >= bs[2] + W - 1) {
+        const int M3 = (int)p->M[2], ncls = bs[2] + W - 1;
+        std::vector<int> tmp;
+        std::vector<long long> ccnt((size_t)ncls + 2);
+        for (long long b = 0; b < nbins; ++b) {
+            const long long c0 = icnt[b], c1 = icnt[b + 1];
+            if (c1 - c0 < 2) continue;
+            const int lo3 = (int)(b % p->nb[2]) * bs[2];
+            auto cls = [&](int s) {
+                int d = lo3 - m0[(size_t)perm[s] * 3 + 2];
+                d += d < 0 ? M3 : 0;
+                d -= d >= M3 ? M3 : 0;
+                const int c = (d < W ? -d : M3 - d) + W - 1;
+                return (c >= 0 && c < ncls) ? c : ncls;
+            };
+            tmp.assign(inc.begin() + c0, inc.begin() + c1);
+            std::fill(ccnt.begin(), ccnt.end(), 0);
+            for (int s : tmp) ccnt[(size_t)cls(s) + 1]++;
+            for (int c = 0; c <= ncls; ++c) ccnt[(size_t)c + 1] += ccnt[(size_t)c];
+            for (int s : tmp) inc[(size_t)(c0 + ccnt[(size_t)cls(s)]++)] = s;
         }
     }
     // subproblems: every bin (empty ones too, they write zeros), chunks of at most kChunk
@@ -570,14 +597,14 @@ int worker_pool(WorkerPool** out) {
 // ---- batched calls in one launch per stage (batch.cu) ----
 
 // Whether the items can share launches: the same kernel width, channel count,
-// spread bin depth and interpolation CTA size; one channel group (K <= 8 and
+// spread bin shape and interpolation CTA size; one channel group (K <= 8 and
 // K <= 32 / W); every grid length served by the two-pass FFT.
 bool fused_eligible(const sdp_work* items, int n) {
     if (n < 1) return false;
     const sdp_plan_s* p0 = items[0].plan;
     for (int i = 0; i < n; ++i) {
         const sdp_plan_s* p = items[i].plan;
-        if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[2] != p0->bs[2] ||
+        if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[0] != p0->bs[0] || p->bs[2] != p0->bs[2] ||
             p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils)
             return false;
         if (p->geo.K > 8 || p->geo.K > 32 / p->geo.W || !mv_width_supported(p->geo.W)) return false;
@@ -697,7 +724,7 @@ int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vect
         const MvUnits usp = units([&](const MvItem& it) {
             return (long long)it.nsub * (it.spread_pairs ? (it.B + 1) / 2 : it.B);
         });
-        SDP_TRY(run(pf, ST_SPREAD, st, [&] { return launch_mv_spread(a, usp, p0->bs[2], p0->geo.W, p0->geo.K, st); }));
+        SDP_TRY(run(pf, ST_SPREAD, st, [&] { return launch_mv_spread(a, usp, p0->bs[0], p0->bs[2], p0->geo.W, p0->geo.K, st); }));
         SDP_TRY(run(pf, ST_ADJ_FFT1, st, [&] { return launch_mv_strided(a, u1, 0, 1, st); }));
         SDP_TRY(run(pf, ST_ADJ_FFT2, st, [&] { return launch_mv_strided(a, u2, 1, 1, st); }));
         SDP_TRY(run(pf, ST_ADJ_FFT3, st, [&] { return launch_mv_epilogue(a, u_fused_adj, st); }));

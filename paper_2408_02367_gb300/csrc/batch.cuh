@@ -61,6 +61,7 @@ cudaError_t launch_mv_prologue(const MvArgs& a, const MvUnits& u, cudaStream_t s
 cudaError_t launch_mv_strided(const MvArgs& a, const MvUnits& u, int axis, int inverse, cudaStream_t st);
 cudaError_t launch_mv_epilogue(const MvArgs& a, const MvUnits& u, cudaStream_t st);
 cudaError_t launch_mv_interp(const MvArgs& a, const MvUnits& u, int W, int threads, cudaStream_t st);
-cudaError_t launch_mv_spread(const MvArgs& a, const MvUnits& u, int bin_depth, int W, int K, cudaStream_t st);
+cudaError_t launch_mv_spread(const MvArgs& a, const MvUnits& u, int bin_width, int bin_depth, int W, int K,
+                             cudaStream_t st);
 
 }  // namespace sdp

@@ -1,12 +1,11 @@
-// Interpolation and spread of several plans in one launch each (the batched
-// forward's last stage and the batched adjoint's first stage; see batch.cu
-// for the layout of a batched launch).  Kernel widths 4 and 6 only: batches
-// of other widths run plan by plan.
+// Interpolation of several plans in one launch (the batched forward's last
+// stage; see batch.cu for the layout of a batched launch and batch_sp.cu for
+// the batched spread).  Kernel widths 4 and 6 only: batches of other widths
+// run plan by plan.
 #include <algorithm>
 
 #include "batch.cuh"
 #include "interp_impl.cuh"
-#include "spread_impl.cuh"
 
 namespace sdp {
 namespace {
@@ -81,49 +80,6 @@ __global__ void __launch_bounds__(NT) mv_interp_kernel(const MvArgs a, const MvU
     MvInterpItems<W, 0>::run(a, u, rl, first, step, lane);
 }
 
-// ---- adjoint: spread, one warp per (subproblem, coil pair) of every item ----
-// u.start holds the prefix sums of nsub * (coil groups) per item.
-template <int B3, int W, int NK>
-__global__ void __launch_bounds__(32, 16) mv_spread_kernel(const MvArgs a, const MvUnits u) {
-    const long long unit = blockIdx.x;
-    const int i = find_item(u, unit);
-    const MvItem& it = a.it[i];
-    const long long local = unit - u.start[i];
-    const int sub = (int)(local % it.nsub);
-    const int by = (int)(local / it.nsub);
-    constexpr int NC2 = spread_coils<B3, NK>();
-    if (NC2 == 2 && it.spread_pairs)
-        spread_body<B3, W, NK, NC2>(it.sa, 0, it.B, sub, by);
-    else
-        spread_body<B3, W, NK, 1>(it.sa, 0, it.B, sub, by);
-}
-
-template <int B3, int W>
-cudaError_t launch_mv_spread_w(const MvArgs& a, const MvUnits& u, int K, cudaStream_t st) {
-    const unsigned grid = (unsigned)u.start[u.n];
-    switch (K) {
-        case 1: mv_spread_kernel<B3, W, 1><<<grid, 32, 0, st>>>(a, u); break;
-        case 2: mv_spread_kernel<B3, W, 2><<<grid, 32, 0, st>>>(a, u); break;
-        case 3: mv_spread_kernel<B3, W, 3><<<grid, 32, 0, st>>>(a, u); break;
-        case 4: mv_spread_kernel<B3, W, 4><<<grid, 32, 0, st>>>(a, u); break;
-        case 5: mv_spread_kernel<B3, W, 5><<<grid, 32, 0, st>>>(a, u); break;
-        case 6: mv_spread_kernel<B3, W, 6><<<grid, 32, 0, st>>>(a, u); break;
-        case 7: mv_spread_kernel<B3, W, 7><<<grid, 32, 0, st>>>(a, u); break;
-        case 8: mv_spread_kernel<B3, W, 8><<<grid, 32, 0, st>>>(a, u); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <int B3>
-cudaError_t launch_mv_spread_b(const MvArgs& a, const MvUnits& u, int W, int K, cudaStream_t st) {
-    switch (W) {
-        case 4: return launch_mv_spread_w<B3, 4>(a, u, K, st);
-        case 6: return launch_mv_spread_w<B3, 6>(a, u, K, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int W, int NT>
 cudaError_t launch_mv_interp_t(const MvArgs& a, const MvUnits& u, cudaStream_t st) {
     int per_sm = 0, dev = 0, nsm = 0;
@@ -156,12 +112,6 @@ cudaError_t launch_mv_interp(const MvArgs& a, const MvUnits& u, int W, int threa
         case 6: return launch_mv_interp_w<6>(a, u, threads, st);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_mv_spread(const MvArgs& a, const MvUnits& u, int bin_depth, int W, int K, cudaStream_t st) {
-    if (u.start[u.n] == 0) return cudaSuccess;
-    if (u.start[u.n] > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return bin_depth == 4 ? launch_mv_spread_b<4>(a, u, W, K, st) : launch_mv_spread_b<8>(a, u, W, K, st);
 }
 
 }  // namespace sdp

@@ -96,7 +96,7 @@ struct SpreadArgs {
 __host__ __device__ constexpr bool spread_pairs_fit(int B3, int NK) { return B3 * NK <= 20; }
 
 // Launch helpers (each returns cudaError_t of the launch).  `pr` may be null.
-// Spread bin shapes with a kernel: 8 x 4 x 8 and 8 x 4 x 4 grid points.
+// Spread bin shapes with a kernel: B1 x 4 x B3 grid points, B1 and B3 each 8 or 4.
 bool spread_bins_supported(const int bs[3]);
 cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,

@@ -1,6 +1,6 @@
 // Adjoint spreading with bins of 8 x 4 x 4 grid points (half-depth register
-// columns: fewer registers per lane, more incidences per sample); the kernel
-// is in spread_impl.cuh.
+// columns: fewer registers per lane, more incidences per sample).
+// The kernel is in spread_impl.cuh.
 #include "spread_impl.cuh"
 
 namespace sdp {
@@ -10,8 +10,8 @@ cudaError_t launch_spread_b4(const Geo& g, const int bs[3], const int nb[3], con
                              const float2* y, const float* scale, int B, int k0, int nk, float2* grids,
                              float2* partials, long long slots_per_b, int* counters, int nbins, int coils,
                              cudaStream_t st) {
-    return launch_spread_depth<4>(g, bs, nb, subs, nsub, inc, pts, tframe, wts, V, y, scale, B, k0, nk, grids,
-                                  partials, slots_per_b, counters, nbins, coils, st);
+    return launch_spread_shape<8, 4>(g, bs, nb, subs, nsub, inc, pts, tframe, wts, V, y, scale, B, k0, nk, grids,
+                                      partials, slots_per_b, counters, nbins, coils, st);
 }
 
 }  // namespace sdp

@@ -3,9 +3,11 @@
 A plan's kernel shapes (include/stodip_op.h, sdp_tuning) do not change what
 the operator computes, only how fast it runs on a given trajectory and volume:
 
-- spread bin depth: 8 x 4 x 8 bins (a lane per 8-point axis-3 column) or
+- spread bin shape: 8 x 4 x 8 bins (a lane per 8-point axis-3 column),
   8 x 4 x 4 bins (half the accumulator registers, so more resident warps, but
-  about 1.3x the (sample, bin) incidences of a W = 4 window);
+  about 1.3x the (sample, bin) incidences of a W = 4 window), or 4 x 4 x 8 and
+  4 x 4 x 4 bins (two incidences per warp step, one per half-warp: more of each
+  multiply-add counts, against more incidences per sample);
 - spread chunk length: incidences per spread CTA (load balance on the dense
   k-space centre against the cost of summing partial tiles);
 - FFT engine: the two-pass register FFTs or the Stockham kernels;
@@ -18,7 +20,9 @@ the operator computes, only how fast it runs on a given trajectory and volume:
   interpolation over the samples (all, or two at a time);
 - the forward prologue with its inputs staged by bulk copies, or loaded directly.
 
-`autotune` builds a plan for every candidate on the caller's geometry, checks
+`autotune` tunes the spread's knobs first and the rest on the fastest spread
+(they are nearly independent).  It builds a plan for every candidate on the
+caller's geometry, checks
 that every candidate's forward and adjoint agree with the first one (they
 compute the same operator; only the order of floating-point sums differs),
 times one operator step (forward of a coil minibatch, then its adjoint) with
@@ -41,31 +45,40 @@ DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_
            "interp_threads": 0, "spread_coils": 0, "interp_run": 0, "interp_coils": 0}
 
 
+SPREAD_BINS = ((8, 4, 8), (8, 4, 4), (4, 4, 8), (4, 4, 4))
+
+
 def candidates(full: bool = False):
-    """The tunings tried: both bin depths x three chunk lengths with the two-pass
-    FFTs, both bin depths with 8 and 4 FFT lines per CTA, 32 and 8 strided FFT
-    columns per CTA, 256-thread interpolation CTAs, one coil per spread warp,
-    and the Stockham engine on the default spread; `full` adds more chunks."""
+    """First round: the spread's knobs with the default FFT and interpolation
+    shapes: every bin shape x three chunk lengths (`full`: five), and one coil
+    per spread warp for the 4-deep bins."""
     chunks = (128, 256, 512, 1024, 2048) if full else (256, 512, 1024)
     out = []
-    for bins in ((8, 4, 8), (8, 4, 4)):
+    for bins in SPREAD_BINS:
         for c in chunks:
             out.append({"spread_bins": bins, "spread_chunk": c, "fft_engine": 0, "fft_lines": 0})
-    for bins in ((8, 4, 8), (8, 4, 4)):
-        for lines in (8, 4):
-            out.append({"spread_bins": bins, "spread_chunk": 512, "fft_engine": 0, "fft_lines": lines})
-    for cols in (32, 8):
-        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "fft_cols": cols})
-    out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 256})
-    out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "spread_coils": 1})
-    for run in (1, 2):
-        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                    "interp_threads": 1024, "interp_run": run, "interp_coils": 2})
-    for threads, run in ((1024, 2), (256, 1)):
-        out.append({"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                    "interp_threads": threads, "interp_run": run, "interp_coils": 2, "fft_staged": 1})
-    out.append({"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 1, "fft_lines": 0})
+    for bins in SPREAD_BINS:
+        if bins[2] == 4:
+            out.append({"spread_bins": bins, "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "spread_coils": 1})
     return out
+
+
+REFINE = [{"fft_lines": 8}, {"fft_lines": 4}, {"fft_lines": 8, "fft_cols": 32}, {"fft_lines": 8, "fft_cols": 8},
+          {"fft_lines": 8, "interp_threads": 256},
+          {"fft_lines": 8, "interp_threads": 1024, "interp_run": 1, "interp_coils": 2},
+          {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2},
+          {"fft_lines": 8, "fft_staged": 1},
+          {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2, "fft_staged": 1},
+          {"fft_lines": 8, "interp_threads": 256, "interp_run": 1, "interp_coils": 2, "fft_staged": 1},
+          {"fft_engine": 1, "fft_lines": 0}]
+
+
+def refinements(spread, variants=REFINE):
+    """Second round, on the spread knobs of the first round's fastest tuning: FFT
+    lines (8, 4) and columns (32, 8) per CTA, interpolation CTA size, run length
+    and coil blocks, the staged prologue, and the Stockham engine."""
+    base = {k: spread[k] for k in ("spread_bins", "spread_chunk", "spread_coils")}
+    return [dict(base, fft_engine=0, **v) if "fft_engine" not in v else dict(base, **v) for v in variants]
 
 
 def _key(omega, frame, n, width, oversamp, V, S, max_batch, B, device):
@@ -82,9 +95,12 @@ def _rel(a, b):
 
 
 def autotune(omega, frame, n, width, oversamp, V, S, max_batch, B=None, cands=None, reps: int = 5,
-             cache: str | None = None, device="cuda", agree: float = 1e-5):
+             cache: str | None = None, device="cuda", agree: float = 1e-5, refine=None):
     """Fastest tuning for this geometry.  Returns (tuning dict, table of
-    {"tuning", "ms", "rel_vs_first"} for every candidate, sorted by time)."""
+    {"tuning", "ms", "rel_vs_first"} for every candidate, sorted by time).
+    Without `cands`, two rounds: the spread's knobs (`candidates()`), then the
+    FFT and interpolation knobs on the fastest spread (`refinements`).  With
+    `cands`, one round unless `refine` lists second-round variants."""
     B = int(max_batch if B is None else B)
     dev = torch.device(device)
     key = _key(omega, frame, n, width, oversamp, V, S, max_batch, B, device)
@@ -95,7 +111,8 @@ def autotune(omega, frame, n, width, oversamp, V, S, max_batch, B=None, cands=No
             e = stored[key]
             best = dict(e["best"], spread_bins=tuple(e["best"]["spread_bins"]))
             return best, e["table"]
-    cands = candidates() if cands is None else cands
+    if cands is None:
+        cands, refine = candidates(), REFINE if refine is None else refine
     K = V.shape[1]
     gen = torch.Generator(device="cpu").manual_seed(12345)
     x = torch.complex(torch.randn((K,) + tuple(n), generator=gen), torch.randn((K,) + tuple(n), generator=gen))
@@ -103,18 +120,19 @@ def autotune(omega, frame, n, width, oversamp, V, S, max_batch, B=None, cands=No
     ci = torch.arange(B, dtype=torch.int32, device=dev) % S.shape[0]
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)     # 256 MB, larger than L2
     table = []
-    ref = None
-    for t in cands:
+    ref = []
+
+    def run(t):
         A = _op.make_operator(omega, frame, n, width, oversamp, V, S, max_batch, device=device, tuning=t)
         y = A.forward(x, ci)
         a = A.adjoint(y, ci)
-        if ref is None:
-            ref = (y.clone(), a.clone())
+        if not ref:
+            ref.append((y.clone(), a.clone(), t))
             rel = 0.0
         else:
-            rel = max(_rel(y, ref[0]), _rel(a, ref[1]))
+            rel = max(_rel(y, ref[0][0]), _rel(a, ref[0][1]))
             if not rel <= agree:
-                raise RuntimeError(f"tuning {t} disagrees with {cands[0]}: rel {rel:.2e}")
+                raise RuntimeError(f"tuning {t} disagrees with {ref[0][2]}: rel {rel:.2e}")
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for i, (e0, e1) in enumerate(evs):
             flush.fill_(float(i))
@@ -127,6 +145,13 @@ def autotune(omega, frame, n, width, oversamp, V, S, max_batch, B=None, cands=No
         table.append({"tuning": dict(A.tuning, spread_bins=list(A.tuning["spread_bins"])), "ms": ms,
                       "rel_vs_first": rel})
         del A
+
+    for t in cands:
+        run(t)
+    if refine:
+        first = min(table, key=lambda r: r["ms"])["tuning"]
+        for t in refinements(dict(first, spread_bins=tuple(first["spread_bins"])), refine):
+            run(t)
     table.sort(key=lambda r: r["ms"])
     best = dict(table[0]["tuning"], spread_bins=tuple(table[0]["tuning"]["spread_bins"]))
     if cache:

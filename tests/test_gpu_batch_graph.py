@@ -23,13 +23,13 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _volume(n, W, sigma, K, C, T, arm_len, seed):
+def _volume(n, W, sigma, K, C, T, arm_len, seed, tuning=None):
     from paper_2408_02367_gb300 import op
     x = synth.ellipsoid_phantom(n, K, seed=seed)
     S = synth.coil_maps(n, C)
     V = synth.subspace_basis(T, K, seed=seed + 10)
     omega, frame = synth.spiral_trajectory(T, 1, arm_len)
-    A = op.make_operator(omega, frame, n, W, sigma, V, S, max_batch=4)
+    A = op.make_operator(omega, frame, n, W, sigma, V, S, max_batch=4, tuning=tuning)
     return A, x
 
 
@@ -147,11 +147,14 @@ def test_one_launch_per_stage_for_a_mixed_size_batch():
         assert v["A"].status() == 0
 
 
-def test_batched_items_beyond_a_plans_workspace_run_in_waves():
+@pytest.mark.parametrize("bins", [(8, 4, 8), (4, 4, 4), (4, 4, 8)])
+def test_batched_items_beyond_a_plans_workspace_run_in_waves(bins):
     """Items of one plan whose minibatches exceed its max_batch together run in waves (one launch
-    set each); accumulate adds into a shared output; results equal the single calls."""
+    set each); accumulate adds into a shared output; results equal the single calls (for every
+    spread bin width)."""
     from paper_2408_02367_gb300 import op
-    A, x = _volume((38, 51, 38), 4, 1.25, 5, 6, 12, 300, 5)      # grid 48 x 64 x 48
+    A, x = _volume((38, 51, 38), 4, 1.25, 5, 6, 12, 300, 5,
+                   tuning={"spread_bins": bins, "spread_chunk": 256})      # grid 48 x 64 x 48
     xt = _t(x)
     cs = [[0, 1, 2], [3, 4], [5], [1, 3, 5, 0]]               # 3 + 2 + 1 + 4 = 10 > max_batch 4
     items = [(A, xt, _t(np.array(c, np.int32)), None) for c in cs]

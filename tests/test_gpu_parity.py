@@ -168,11 +168,16 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "interp_threads": 1024, "interp_run": 2,
      "interp_coils": 2},
     {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "interp_run": 8, "interp_coils": 1},
+    {"spread_bins": (4, 4, 4), "spread_chunk": 64, "fft_engine": 0},
+    {"spread_bins": (4, 4, 8), "spread_chunk": 32, "fft_engine": 0},
+    {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "spread_coils": 1},
+    {"spread_bins": (4, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
-    """Every tuning computes the same operator: half-depth spread bins, short spread
-    chunks (many multi-chunk bins), one or two coils per spread warp (three coils:
-    a pair and an odd tail) and the Stockham FFT engine, forward and adjoint."""
+    """Every tuning computes the same operator: half-depth spread bins, 4 x 4 bins (two
+    incidences per warp step), short spread chunks (many multi-chunk bins), one or two
+    coils per spread warp (three coils: a pair and an odd tail) and the Stockham FFT
+    engine, forward and adjoint."""
     from paper_2408_02367_gb300 import op
     c = make_case((20, 18, 16), 4, 1.25, 3, 3, 10, 1, 600, [2, 0, 1])
     geo = O.Geometry(c["n"], 4, 1.25)
@@ -186,6 +191,41 @@ def test_tuned_kernel_shapes_match_oracle(tuning):
     a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
     assert_close(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
                  f"{tuning} adjoint")
+    assert A.status() == 0
+
+
+@pytest.mark.parametrize("bins", [(8, 4, 8), (8, 4, 4), (4, 4, 8), (4, 4, 4)])
+def test_spread_bins_on_a_short_axis3_grid(bins):
+    """A 4-point image axis at W=6 gets a 12-point axis-3 grid, shorter than an 8-deep bin
+    plus a window (B3 + W - 1 = 13): a window can meet a bin in two pieces along axis 3, and
+    the spread then runs every position of the column instead of one class's run.  4-deep
+    bins still fit (9 <= 12) and take the class runs on a grid of three bins.  The adjoint
+    matches the oracle either way."""
+    from paper_2408_02367_gb300 import op
+    c = make_case((16, 12, 4), 6, 2.0, 5, 2, 6, 1, 300, [1, 0, 1])
+    geo = O.Geometry(c["n"], 6, 2.0)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], 6, 2.0, c["V"], c["S"], max_batch=3,
+                         tuning={"spread_bins": bins, "spread_chunk": 64})
+    assert A.grid[2] == 12 and (A.grid[2] < bins[2] + 6 - 1) == (bins[2] == 8)
+    r = synth.random_complex((3, A.J), 5)
+    a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
+    assert_close(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
+                 f"{bins} short axis 3 adjoint")
+    assert A.status() == 0
+
+
+def test_half_warp_bins_with_channel_groups():
+    """4 x 4 x 4 bins with K=10 channels: a group of 8 (one coil per warp) and a group of 2
+    (coil pairs), 8-byte column stores, short chunks; three coils."""
+    from paper_2408_02367_gb300 import op
+    c = make_case((16, 16, 16), 4, 1.25, 10, 2, 12, 1, 400, [0, 1, 1])
+    geo = O.Geometry(c["n"], 4, 1.25)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3,
+                         tuning={"spread_bins": (4, 4, 4), "spread_chunk": 64})
+    r = synth.random_complex((3, A.J), 6)
+    a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
+    assert_close(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
+                 "4x4x4 bins, K=10 adjoint")
     assert A.status() == 0
 
 
