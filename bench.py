@@ -443,6 +443,7 @@ WHOLE_BRAIN_REFINE = [
     {"fft_lines": 8, "interp_threads": 1024, "interp_coils": 2, "interp_run": 2},
     {"fft_lines": 8, "interp_threads": 256, "interp_coils": 2},
     {"fft_lines": 8, "interp_threads": 1024, "fft_staged": 1},
+    {"fft_lines": 8, "interp_tiled": 1},
 ]
 
 

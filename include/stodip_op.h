@@ -127,8 +127,10 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  * computes the same operator; they differ in speed and in the order of
  * floating-point sums only.
  *   spread_bins   grid points per spread bin (axis 1, 2, 3): {8, 4, 8} (default,
- *                 a lane per 8-point axis-3 column) or {8, 4, 4} (half-depth
- *                 columns: fewer registers per lane, more incidences per sample).
+ *                 a lane per 8-point axis-3 column), {8, 4, 4} (half-depth
+ *                 columns: fewer registers per lane, more incidences per sample),
+ *                 {4, 4, 8} or {4, 4, 4} (16 columns, two lanes per column, the
+ *                 two half-warps taking alternate incidences).
  *   spread_chunk  incidences per spread subproblem, 32 .. 65536 (default 512):
  *                 bounds the work of one CTA on the dense k-space centre.
  *   fft_engine    0: two-pass register FFTs where the length has one (default),
@@ -165,6 +167,13 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 CTAs, whole image rows per unit): 0 (default: off) or 1 (on
  *                 where supported: a two-pass length, even N3, 16-byte aligned
  *                 x and S; elsewhere the direct-load kernels run).
+ *   interp_tiled  interpolation from shared-memory tiles: 0 (default: off, the
+ *                 row kernel) or 1 (on where supported: W = 2 or 4 and at most 8
+ *                 channels per call; elsewhere the row kernel).  The plan orders
+ *                 the samples by tiles of 8^3 grid points either way; the tiled
+ *                 kernel copies each tile's grid with its window margin into
+ *                 shared memory once per coil and interpolates the tile's samples
+ *                 from there.  The batched calls run such plans plan by plan.
  */
 typedef struct {
     int32_t spread_bins[3];
@@ -177,6 +186,7 @@ typedef struct {
     int32_t interp_run;
     int32_t interp_coils;
     int32_t fft_staged;
+    int32_t interp_tiled;
 } sdp_tuning;
 
 /*

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstodip_op.so")
-SOURCES = ["api.cu", "fft.cu", "fft2.cu", "interp.cu", "spread.cu", "spread_b4.cu", "spread_4x4x8.cu", "spread_4x4x4.cu",
+SOURCES = ["api.cu", "fft.cu", "fft2.cu", "interp.cu", "interp_tiles.cu", "spread.cu", "spread_b4.cu", "spread_4x4x8.cu", "spread_4x4x4.cu",
            "loss.cu", "noalloc.cu", "tv.cu", "dm.cu", "batch.cu", "batch_nu.cu", "batch_sp.cu", "fft2_staged.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

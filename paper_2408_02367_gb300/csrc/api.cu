@@ -48,6 +48,9 @@ struct sdp_plan_s {
     int spread_coils = 0;     // coils per spread warp: 0 = two where they fit, 1 = one
     int interp_run = 1;       // consecutive samples per interpolation warp run
     int interp_coils = 0;     // coils per interpolation sweep over the samples: 0 = all
+    int interp_tiled = 0;     // 1: the tiled interpolation where it has a kernel (interp_tiles.cu)
+    int nt[3] = {0, 0, 0};    // interpolation tiles per axis
+    int n_itiles = 0;         // tiled interpolation work items
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -62,6 +65,7 @@ struct sdp_plan_s {
     float2* tw = nullptr;    // [M1 | M2 | M3]
     int* inc = nullptr;
     SubProb* subs = nullptr;
+    int4* itiles = nullptr;  // tiled interpolation work items (flat tile index, first sample, count, 0), heaviest first
     float2* partials = nullptr;
     int* counters = nullptr;
     int* status = nullptr;
@@ -219,6 +223,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     p->spread_coils = tn ? tn->spread_coils : 0;
     p->interp_run = (tn && tn->interp_run) ? tn->interp_run : 1;
     p->interp_coils = tn ? tn->interp_coils : 0;
+    p->interp_tiled = tn ? tn->interp_tiled : 0;
 
     // ---- host tables ----
     std::vector<float> dinv(p->n[0] + p->n[1] + p->n[2]);
@@ -265,31 +270,60 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     if (nbins >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
     p->nbins = (int)nbins;
 
-    // window start and the bin of each sample (bin of the sample's own coordinate)
+    // window start of each sample, and its sort key: samples are ordered by interpolation
+    // tile (tiles of kTile^3 grid points: the tiled interpolation takes a tile's samples as
+    // one range), then by spread bin within the tile (bins nest in tiles: kTile is a
+    // multiple of every bin edge), both of the sample's own coordinate
     const float halfW = (float)(0.5 * W);
+    const int kTile = interp_tile_edge();
+    int bpt[3];
+    for (int a = 0; a < 3; ++a) {
+        bpt[a] = kTile / bs[a];
+        p->nt[a] = (int)((p->M[a] + kTile - 1) / kTile);
+    }
+    const long long BPT = (long long)bpt[0] * bpt[1] * bpt[2];
+    const long long ntiles = (long long)p->nt[0] * p->nt[1] * p->nt[2];
+    const long long nkeys = ntiles * BPT;
     std::vector<int> m0((size_t)J * 3);
-    std::vector<long long> sbin((size_t)J);
+    std::vector<long long> skey((size_t)J);
     for (long long j = 0; j < J; ++j) {
-        long long bi = 0;
+        long long ti = 0, li = 0;
         for (int a = 0; a < 3; ++a) {
             const float gv = gc[(size_t)j * 3 + a];
             const float tt = gv - halfW;
             m0[(size_t)j * 3 + a] = (int)std::ceil(tt);
             int ba = (int)(gv / (float)bs[a]);
             if (ba >= p->nb[a]) ba = p->nb[a] - 1;
-            bi = bi * p->nb[a] + ba;
+            ti = ti * p->nt[a] + ba / bpt[a];
+            li = li * bpt[a] + ba % bpt[a];
         }
-        sbin[j] = bi;
+        skey[j] = ti * BPT + li;
     }
-    // stable counting sort of samples by bin
-    std::vector<long long> cnt(nbins + 1, 0);
-    for (long long j = 0; j < J; ++j) cnt[sbin[j] + 1]++;
-    for (long long b = 0; b < nbins; ++b) cnt[b + 1] += cnt[b];
+    // stable counting sort of samples by key
+    std::vector<long long> cnt((size_t)nkeys + 1, 0);
+    for (long long j = 0; j < J; ++j) cnt[(size_t)skey[j] + 1]++;
+    for (long long b = 0; b < nkeys; ++b) cnt[(size_t)b + 1] += cnt[(size_t)b];
     std::vector<int> perm((size_t)J);   // sorted position -> original sample
     {
         std::vector<long long> cur(cnt.begin(), cnt.end() - 1);
-        for (long long j = 0; j < J; ++j) perm[cur[sbin[j]]++] = (int)j;
+        for (long long j = 0; j < J; ++j) perm[(size_t)cur[(size_t)skey[j]]++] = (int)j;
     }
+    // the tiled interpolation's work items (flattened tile index, first sorted sample,
+    // count), heaviest first: every non-empty tile, a dense one (the k-space centre holds
+    // tiles of thousands of samples) cut into near-equal pieces of at most kTileItem
+    // samples, each of which copies the tile's grid once per coil
+    constexpr long long kTileItem = 512;
+    std::vector<int4> itiles;
+    for (long long t = 0; t < ntiles; ++t) {
+        const long long c0 = cnt[(size_t)(t * BPT)], c1 = cnt[(size_t)((t + 1) * BPT)];
+        const long long n = c1 - c0, parts = (n + kTileItem - 1) / kTileItem;
+        for (long long q = 0; q < parts; ++q) {
+            const long long a = c0 + n * q / parts, b = c0 + n * (q + 1) / parts;
+            itiles.push_back(make_int4((int)t, (int)a, (int)(b - a), 0));
+        }
+    }
+    std::stable_sort(itiles.begin(), itiles.end(), [](const int4& a, const int4& b) { return a.z > b.z; });
+    p->n_itiles = (int)itiles.size();
     std::vector<float4> pts((size_t)J);
     std::vector<int> tf((size_t)J);
     for (long long s = 0; s < J; ++s) {
@@ -423,6 +457,7 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     SDP_TRY(dev_alloc(p, &p->tw, tw.size()));
     SDP_TRY(dev_alloc(p, &p->inc, inc.size()));
     SDP_TRY(dev_alloc(p, &p->subs, subs.size()));
+    SDP_TRY(dev_alloc(p, &p->itiles, std::max<size_t>(itiles.size(), 1)));
     const size_t P = (size_t)bs[0] * bs[1] * bs[2];
     SDP_TRY(dev_alloc(p, &p->partials, (size_t)std::max(slots, 1LL) * P * Kz * p->maxB));
     SDP_TRY(dev_alloc(p, &p->counters, (size_t)nbins * p->maxB * ((K + 7) / 8)));
@@ -448,6 +483,8 @@ int build_plan(sdp_plan_s* p, const sdp_plan_desc* d, const sdp_tuning* tn, cuda
     SDP_CUDA(cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->inc, inc.data(), inc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(SubProb), cudaMemcpyHostToDevice, st));
+    if (!itiles.empty())
+        SDP_CUDA(cudaMemcpyAsync(p->itiles, itiles.data(), itiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     SDP_CUDA(cudaMemsetAsync(p->counters, 0, (size_t)nbins * p->maxB * ((K + 7) / 8) * sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
     SDP_CUDA(cudaMemsetAsync(p->loss_counter, 0, sizeof(unsigned int), st));
@@ -514,6 +551,19 @@ int check_call(const sdp_plan_s* p, const void* in, const int32_t* coil_idx, int
     return SDP_OK;
 }
 
+// Step A3 of the plan: the tiled interpolation where the plan asks for it and a kernel
+// exists for the width and channel count, else the row kernel.
+cudaError_t plan_interp(const sdp_plan_s* p, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
+                        cudaStream_t st) {
+    const Geo& g = p->geo;
+    // (grids of at least 16 points per axis: a tile with its margin then wraps at most once)
+    if (p->interp_tiled && interp_tiles_supported(g.W, nk) && g.M[0] >= 16 && g.M[1] >= 16 && g.M[2] >= 16)
+        return launch_interp_tiles(g, p->itiles, p->n_itiles, p->nt[1], p->nt[2], p->pts, p->tframe, p->wts, p->V,
+                                   grids, B, k0, nk, y, accumulate, p->status, st);
+    return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, grids,
+                         B, k0, nk, y, accumulate, st);
+}
+
 int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, int k0, int nk, void* y,
                  int accumulate, cudaStream_t st) {
     SDP_TRY(check_call(p, x, coil_idx, B, k0, nk, y));
@@ -532,8 +582,7 @@ int forward_impl(sdp_plan_s* p, const void* x, const int32_t* coil_idx, int B, i
         return launch_fft_strided(p->ax[0], 0, p->bufB, p->bufA, (int)N1, 1, (int)M1, 0, M2 * M3 * nk, B, st);
     }));
     SDP_TRY(run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, p->bufA, B, k0, nk,
-                             static_cast<float2*>(y), accumulate, st);
+        return plan_interp(p, p->bufA, B, k0, nk, static_cast<float2*>(y), accumulate, st);
     }));
     return SDP_OK;
 }
@@ -597,15 +646,16 @@ int worker_pool(WorkerPool** out) {
 // ---- batched calls in one launch per stage (batch.cu) ----
 
 // Whether the items can share launches: the same kernel width, channel count,
-// spread bin shape and interpolation CTA size; one channel group (K <= 8 and
-// K <= 32 / W); every grid length served by the two-pass FFT.
+// spread bin shape and interpolation CTA size, the row interpolation (plans with
+// the tiled one run plan by plan); one channel group (K <= 8 and K <= 32 / W);
+// every grid length served by the two-pass FFT.
 bool fused_eligible(const sdp_work* items, int n) {
     if (n < 1) return false;
     const sdp_plan_s* p0 = items[0].plan;
     for (int i = 0; i < n; ++i) {
         const sdp_plan_s* p = items[i].plan;
         if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[0] != p0->bs[0] || p->bs[2] != p0->bs[2] ||
-            p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils)
+            p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils || p->interp_tiled)
             return false;
         if (p->geo.K > 8 || p->geo.K > 32 / p->geo.W || !mv_width_supported(p->geo.W)) return false;
         for (int a = 0; a < 3; ++a)
@@ -856,7 +906,8 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
             tn->spread_coils < 0 || tn->spread_coils > 2 ||
             (tn->interp_run != 0 && tn->interp_run != 1 && tn->interp_run != 2 && tn->interp_run != 4 &&
              tn->interp_run != 8) ||
-            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch || tn->fft_staged < 0 || tn->fft_staged > 1)
+            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch || tn->fft_staged < 0 || tn->fft_staged > 1 ||
+            tn->interp_tiled < 0 || tn->interp_tiled > 1)
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;
     }
@@ -954,8 +1005,7 @@ int sdp_gram_samples(sdp_plan_t p, const void* y, int32_t B, void* out, void* st
                              p->counters, p->nbins, p->spread_coils, st);
     }));
     return run(p, ST_INTERP, st, [&] {
-        return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, p->bufA, B, 0, g.K,
-                             static_cast<float2*>(out), 0, st);
+        return plan_interp(p, p->bufA, B, 0, g.K, static_cast<float2*>(out), 0, st);
     });
 }
 
@@ -1013,6 +1063,7 @@ int sdp_plan_tuning(sdp_plan_t p, sdp_tuning* out) {
     out->interp_run = p->interp_run;
     out->interp_coils = p->interp_coils;
     out->fft_staged = p->ax[2].staged;
+    out->interp_tiled = p->interp_tiled;
     return SDP_OK;
 }
 

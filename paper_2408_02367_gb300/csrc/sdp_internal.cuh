@@ -112,6 +112,15 @@ cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const floa
 // Kaiser-Bessel weights of every (sorted) sample: wts[s][d][a] = phi(g_d - (m0_d + a)),
 // m0_d = ceil(g_d - W/2) in float32; computed once per plan.
 cudaError_t launch_kb_weights(const Geo& g, const float4* pts, float* wts, cudaStream_t st);
+// Tiled interpolation (interp_tiles.cu): samples ordered by tiles of
+// interp_tile_edge()^3 grid points; `tiles` lists work items (flattened tile
+// index over nt1 x nt2 x nt3, first sample, count, 0), a dense tile's samples
+// split over several items.
+int interp_tile_edge();
+bool interp_tiles_supported(int W, int nk);
+cudaError_t launch_interp_tiles(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
+                                const int* tframe, const float* wts, const float2* V, const float2* grids, int B,
+                                int k0, int nk, float2* y, int accumulate, int* status, cudaStream_t st);
 cudaError_t launch_interp(const Geo& g, int threads, int run, int cblock, const float4* pts, const int* tframe,
                           const float* wts,
                           const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,

@@ -65,12 +65,14 @@ class Tuning(ctypes.Structure):
         ("interp_run", ctypes.c_int32),
         ("interp_coils", ctypes.c_int32),
         ("fft_staged", ctypes.c_int32),
+        ("interp_tiled", ctypes.c_int32),
     ]
 
     @staticmethod
     def of(d):
         """From a dict {spread_bins: (8, 4, 8), spread_chunk: 512, fft_engine: 0, fft_lines: 0, fft_cols: 0,
-        interp_threads: 0, spread_coils: 0, interp_run: 0, interp_coils: 0}; missing keys take those defaults."""
+        interp_threads: 0, spread_coils: 0, interp_run: 0, interp_coils: 0, fft_staged: 0, interp_tiled: 0};
+        missing keys take those defaults."""
         t = Tuning()
         t.spread_bins = (ctypes.c_int32 * 3)(*[int(v) for v in d.get("spread_bins", (8, 4, 8))])
         t.spread_chunk = int(d.get("spread_chunk", 512))
@@ -82,6 +84,7 @@ class Tuning(ctypes.Structure):
         t.interp_run = int(d.get("interp_run", 0))
         t.interp_coils = int(d.get("interp_coils", 0))
         t.fft_staged = int(d.get("fft_staged", 0))
+        t.interp_tiled = int(d.get("interp_tiled", 0))
         return t
 
     def as_dict(self):
@@ -89,7 +92,7 @@ class Tuning(ctypes.Structure):
                 "fft_engine": int(self.fft_engine), "fft_lines": int(self.fft_lines), "fft_cols": int(self.fft_cols),
                 "interp_threads": int(self.interp_threads), "spread_coils": int(self.spread_coils),
                 "interp_run": int(self.interp_run), "interp_coils": int(self.interp_coils),
-                "fft_staged": int(self.fft_staged)}
+                "fft_staged": int(self.fft_staged), "interp_tiled": int(self.interp_tiled)}
 
 
 class Work(ctypes.Structure):

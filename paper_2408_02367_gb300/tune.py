@@ -18,7 +18,8 @@ the operator computes, only how fast it runs on a given trajectory and volume:
   their register columns fit, or one);
 - consecutive samples per interpolation warp run, and coils per sweep of the
   interpolation over the samples (all, or two at a time);
-- the forward prologue with its inputs staged by bulk copies, or loaded directly.
+- the forward prologue with its inputs staged by bulk copies, or loaded directly;
+- the interpolation from shared-memory tiles, or the row kernel's gathers.
 
 `autotune` tunes the spread's knobs first and the rest on the fastest spread
 (they are nearly independent).  It builds a plan for every candidate on the
@@ -42,7 +43,8 @@ import torch
 from . import op as _op
 
 DEFAULT = {"spread_bins": (8, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 0, "fft_cols": 0,
-           "interp_threads": 0, "spread_coils": 0, "interp_run": 0, "interp_coils": 0}
+           "interp_threads": 0, "spread_coils": 0, "interp_run": 0, "interp_coils": 0, "fft_staged": 0,
+           "interp_tiled": 0}
 
 
 SPREAD_BINS = ((8, 4, 8), (8, 4, 4), (4, 4, 8), (4, 4, 4))
@@ -70,13 +72,15 @@ REFINE = [{"fft_lines": 8}, {"fft_lines": 4}, {"fft_lines": 8, "fft_cols": 32}, 
           {"fft_lines": 8, "fft_staged": 1},
           {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2, "fft_staged": 1},
           {"fft_lines": 8, "interp_threads": 256, "interp_run": 1, "interp_coils": 2, "fft_staged": 1},
+          {"fft_lines": 8, "interp_tiled": 1}, {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 1},
           {"fft_engine": 1, "fft_lines": 0}]
 
 
 def refinements(spread, variants=REFINE):
     """Second round, on the spread knobs of the first round's fastest tuning: FFT
     lines (8, 4) and columns (32, 8) per CTA, interpolation CTA size, run length
-    and coil blocks, the staged prologue, and the Stockham engine."""
+    and coil blocks, the tiled interpolation, the staged prologue, and the
+    Stockham engine."""
     base = {k: spread[k] for k in ("spread_bins", "spread_chunk", "spread_coils")}
     return [dict(base, fft_engine=0, **v) if "fft_engine" not in v else dict(base, **v) for v in variants]
 

@@ -172,6 +172,8 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (4, 4, 8), "spread_chunk": 32, "fft_engine": 0},
     {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "spread_coils": 1},
     {"spread_bins": (4, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024},
+    {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "interp_tiled": 1},
+    {"spread_bins": (8, 4, 8), "spread_chunk": 64, "fft_engine": 0, "interp_tiled": 1, "fft_staged": 1},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, 4 x 4 bins (two
@@ -226,6 +228,35 @@ def test_half_warp_bins_with_channel_groups():
     a = A.adjoint(t(r), t(c["coils"])).cpu().numpy()
     assert_close(a, O.gridding_adjoint(geo, r, c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
                  "4x4x4 bins, K=10 adjoint")
+    assert A.status() == 0
+
+
+@pytest.mark.parametrize("n,W,sigma,K,coils", [((40, 36, 44), 4, 1.25, 5, [2, 0, 1]),
+                                               ((24, 20, 16), 2, 2.0, 8, [1, 0]),
+                                               ((20, 18, 16), 6, 2.0, 3, [0, 1]),
+                                               ((18, 16, 12), 4, 1.25, 10, [1, 0])])
+def test_tiled_interpolation_matches_oracle(n, W, sigma, K, coils):
+    """The tiled interpolation (8^3 tiles with their window margin in shared memory): W=4 with
+    partial edge tiles and three coils, W=2 with 8 channels, and the row kernel where the tiled one
+    has no kernel (W=6; K=10 > 8 channels per call), all with interp_tiled=1; plus a channel
+    subset (k0 > 0) and accumulate into an existing output."""
+    from paper_2408_02367_gb300 import op
+    c = make_case(n, W, sigma, K, 3, 12, 1, 500, coils)
+    geo = O.Geometry(c["n"], W, sigma)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], W, sigma, c["V"], c["S"], max_batch=3,
+                         tuning={"interp_tiled": 1})
+    assert A.tuning["interp_tiled"] == 1
+    y = A.forward(t(c["x"]), t(c["coils"])).cpu().numpy()
+    assert_close(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
+                 f"tiled interpolation n={n} W={W} K={K}")
+    if K >= 3:
+        # channels 1 .. K-2 added onto a copy of the channel-0 and channel-(K-1) parts
+        ci = t(c["coils"])
+        xs = t(c["x"])
+        yk = A.forward(xs, ci, k0=0, nk=1)
+        A.forward(xs, ci, out=yk, accumulate=True, k0=K - 1, nk=1)
+        A.forward(xs, ci, out=yk, accumulate=True, k0=1, nk=K - 2)
+        assert_close(yk.cpu().numpy(), y, FP32_BOUND, "tiled interpolation, channel subsets")
     assert A.status() == 0
 
 
@@ -388,7 +419,7 @@ def test_staged_prologue_equals_direct_prologue(n, K, coils):
     a multiply-add differently, so agreement is to float32 rounding, not bits), on grid lengths
     160, 80, 200, 250 and with an odd N3 (where the direct kernel runs)."""
     from paper_2408_02367_gb300 import op
-    c = make_case(n, 4, 1.25, K, 2, 6, 1, 300, coils)
+    c = make_case(n, 4, 1.25, K, 2, 12, 1, 300, coils)     # 12 frames: a rank-K subspace for K <= 8
     geo = O.Geometry(c["n"], 4, 1.25)
     base = {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8}
     A0 = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3, tuning=base)
