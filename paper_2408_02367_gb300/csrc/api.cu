@@ -551,13 +551,20 @@ int check_call(const sdp_plan_s* p, const void* in, const int32_t* coil_idx, int
     return SDP_OK;
 }
 
+// Whether step A3 of a call with nk channels runs the tiled interpolation: the plan
+// asks for it, a kernel exists for the width and channel count, and every grid axis
+// has at least 16 points (a tile with its margin then wraps around it at most once).
+bool plan_interp_tiled(const sdp_plan_s* p, int nk) {
+    const Geo& g = p->geo;
+    return p->interp_tiled && interp_tiles_supported(g.W, nk) && g.M[0] >= 16 && g.M[1] >= 16 && g.M[2] >= 16;
+}
+
 // Step A3 of the plan: the tiled interpolation where the plan asks for it and a kernel
 // exists for the width and channel count, else the row kernel.
 cudaError_t plan_interp(const sdp_plan_s* p, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,
                         cudaStream_t st) {
     const Geo& g = p->geo;
-    // (grids of at least 16 points per axis: a tile with its margin then wraps at most once)
-    if (p->interp_tiled && interp_tiles_supported(g.W, nk) && g.M[0] >= 16 && g.M[1] >= 16 && g.M[2] >= 16)
+    if (plan_interp_tiled(p, nk))
         return launch_interp_tiles(g, p->itiles, p->n_itiles, p->nt[1], p->nt[2], p->pts, p->tframe, p->wts, p->V,
                                    grids, B, k0, nk, y, accumulate, p->status, st);
     return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, grids,
@@ -646,16 +653,17 @@ int worker_pool(WorkerPool** out) {
 // ---- batched calls in one launch per stage (batch.cu) ----
 
 // Whether the items can share launches: the same kernel width, channel count,
-// spread bin shape and interpolation CTA size, the row interpolation (plans with
-// the tiled one run plan by plan); one channel group (K <= 8 and K <= 32 / W);
-// every grid length served by the two-pass FFT.
+// spread bin shape and interpolation kernel (CTA size, tiled or not); one
+// channel group (K <= 8 and K <= 32 / W); every grid length served by the
+// two-pass FFT.
 bool fused_eligible(const sdp_work* items, int n) {
     if (n < 1) return false;
     const sdp_plan_s* p0 = items[0].plan;
     for (int i = 0; i < n; ++i) {
         const sdp_plan_s* p = items[i].plan;
         if (p->geo.W != p0->geo.W || p->geo.K != p0->geo.K || p->bs[0] != p0->bs[0] || p->bs[2] != p0->bs[2] ||
-            p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils || p->interp_tiled)
+            p->interp_threads != p0->interp_threads || p->interp_coils != p0->interp_coils ||
+            p->interp_tiled != p0->interp_tiled)
             return false;
         if (p->geo.K > 8 || p->geo.K > 32 / p->geo.W || !mv_width_supported(p->geo.W)) return false;
         for (int a = 0; a < 3; ++a)
@@ -672,6 +680,7 @@ int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vect
     std::memset(&a, 0, sizeof(a));
     const int n = (int)idx.size();
     const sdp_plan_s* p0 = items[idx[0]].plan;
+    bool tiled = true;   // every item's interpolation tiled (the plans agree on asking for it)
     for (int q = 0; q < n; ++q) {
         const sdp_work& w = items[idx[q]];
         sdp_plan_s* p = w.plan;
@@ -738,6 +747,11 @@ int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vect
         it.nsub = p->nsub;
         it.spread_pairs = (spread_pairs_fit(p->bs[2], g.K) && p->spread_coils != 1 && w.B >= 2) ? 1 : 0;
         it.interp_coils = p->interp_coils > 0 && p->interp_coils < w.B ? p->interp_coils : w.B;
+        it.itiles = p->itiles;
+        it.n_itiles = p->n_itiles;
+        it.nt2 = p->nt[1];
+        it.nt3 = p->nt[2];
+        tiled = tiled && plan_interp_tiled(p, g.K);
     }
     // units of each stage
     auto units = [&](auto count) {
@@ -764,11 +778,15 @@ int run_wave(const sdp_work* items, const std::vector<int>& idx, const std::vect
     sdp_plan_s* pf = items[idx[0]].plan;
     if (!adjoint) {
         const MvUnits u2 = u_strided(1), u1 = u_strided(0);
-        const MvUnits us = units([&](const MvItem& it) { return (long long)it.g.J; });
+        const MvUnits us = tiled ? units([&](const MvItem& it) { return (long long)it.n_itiles; })
+                                 : units([&](const MvItem& it) { return (long long)it.g.J; });
         SDP_TRY(run(pf, ST_FWD_FFT3, st, [&] { return launch_mv_prologue(a, u_fused_fwd, st); }));
         SDP_TRY(run(pf, ST_FWD_FFT2, st, [&] { return launch_mv_strided(a, u2, 1, 0, st); }));
         SDP_TRY(run(pf, ST_FWD_FFT1, st, [&] { return launch_mv_strided(a, u1, 0, 0, st); }));
-        SDP_TRY(run(pf, ST_INTERP, st, [&] { return launch_mv_interp(a, us, p0->geo.W, p0->interp_threads, st); }));
+        SDP_TRY(run(pf, ST_INTERP, st, [&] {
+            return tiled ? launch_mv_interp_tiles(a, us, p0->geo.W, p0->geo.K, st)
+                         : launch_mv_interp(a, us, p0->geo.W, p0->interp_threads, st);
+        }));
     } else {
         const MvUnits u1 = u_strided(0), u2 = u_strided(1);
         const MvUnits usp = units([&](const MvItem& it) {

@@ -41,6 +41,9 @@ struct MvItem {
     int nsub;
     int spread_pairs;         // 1: one spread warp holds two coils
     int interp_coils;         // coils per interpolation sweep over the samples (B: all at once)
+    const int4* itiles;       // tiled interpolation: the plan's work items, their count, tiles per axis 2, 3
+    int n_itiles;
+    int nt2, nt3;
 };
 
 struct MvArgs {
@@ -61,6 +64,8 @@ cudaError_t launch_mv_prologue(const MvArgs& a, const MvUnits& u, cudaStream_t s
 cudaError_t launch_mv_strided(const MvArgs& a, const MvUnits& u, int axis, int inverse, cudaStream_t st);
 cudaError_t launch_mv_epilogue(const MvArgs& a, const MvUnits& u, cudaStream_t st);
 cudaError_t launch_mv_interp(const MvArgs& a, const MvUnits& u, int W, int threads, cudaStream_t st);
+// Tiled interpolation of several plans (interp_tiles.cu); u.start: prefix sums of work items.
+cudaError_t launch_mv_interp_tiles(const MvArgs& a, const MvUnits& u, int W, int K, cudaStream_t st);
 cudaError_t launch_mv_spread(const MvArgs& a, const MvUnits& u, int bin_width, int bin_depth, int W, int K,
                              cudaStream_t st);
 

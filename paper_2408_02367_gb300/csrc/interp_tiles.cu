@@ -29,6 +29,7 @@
 // Widths 2 and 4, up to 8 channels per call; other calls use interp.cu.
 #include <atomic>
 
+#include "batch.cuh"
 #include "interp_impl.cuh"
 #include "tma.cuh"
 
@@ -55,6 +56,142 @@ struct TileDims {
     static constexpr int SMEM = BYTES + 16;   // the tile and the copies' mbarrier
 };
 
+// One work item td = (flattened tile index, first sample, sample count, -): for each
+// coil the item's tile is copied into sg (bulk copies completing on bar, or cp.async),
+// then the item's samples are interpolated from it.  False if a copy did not land
+// within the wait's bound (status then holds SDP_ERR_TIMEOUT and the caller leaves).
+template <int W, int NK>
+__device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, int nt3,
+                                          const float4* __restrict__ pts, const int* __restrict__ tframe,
+                                          const float* __restrict__ wts, const float2* __restrict__ V,
+                                          const float2* __restrict__ grids, int B, int k0, float2* __restrict__ y,
+                                          int accumulate, int* status, float2* sg, uint64_t* bar, uint32_t& phase) {
+    using D = TileDims<W, NK>;
+    constexpr int H = D::H, ROW = D::ROW, PLANE = D::PLANE;
+    constexpr int NWARP = kTileThreads / 32;
+    constexpr int HW = W / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4, l16 = lane & 15;
+    const bool act = l16 < W * W;
+    const int a2 = act ? l16 / W : 0, a3 = act ? l16 % W : 0;   // idle lanes repeat tap (0, 0) with zero weight
+    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+    const long long Gk = (long long)M1 * M2 * M3 * NK;
+    const long long J = g.J;
+    const int t3 = td.x % nt3, t12 = td.x / nt3;
+    const int t2 = t12 % nt2, t1 = t12 / nt2;
+    const int lo1 = t1 * kTile - HW, lo2 = t2 * kTile - HW, lo3 = t3 * kTile - HW;
+    const int start = td.y, count = td.z;
+    // a row's H points along axis 3 start at p0 and run la points before they wrap
+    // around the grid (la = H unless the tile crosses the grid's end along axis 3)
+    const int p0 = wrap1(lo3, M3);
+    const int la = M3 - p0 < H ? M3 - p0 : H;
+    for (int b = 0; b < B; ++b) {
+        __syncthreads();   // the previous pass's readers are done with sg
+        const float2* gb = grids + (long long)b * Gk;
+        // Bulk copies, one per row piece (one or two pieces per row), where every
+        // piece starts on a 16-byte boundary (p0 NK and la NK even, the grid aligned:
+        // W = 4 tiles always); else cp.async 8 bytes per value.
+        const bool bulk = ((p0 * NK) & 1) == 0 && ((la * NK) & 1) == 0 &&
+                          (reinterpret_cast<unsigned long long>(gb) & 15) == 0;
+        if (bulk) {
+            if (threadIdx.x == 0) tma::mbar_expect_tx(bar, (uint32_t)D::BYTES);
+            __syncthreads();   // the expected bytes are registered before any copy lands
+            for (int r = threadIdx.x; r < H * H; r += kTileThreads) {
+                const int h1 = r / H, h2 = r - h1 * H;
+                const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
+                float2* dst = sg + r * ROW;
+                tma::bulk_g2s(dst, src + (long long)p0 * NK, (uint32_t)(la * NK * 8), bar);
+                if (la < H) tma::bulk_g2s(dst + la * NK, src, (uint32_t)((H - la) * NK * 8), bar);
+            }
+            const bool landed = __syncthreads_and(tma::mbar_wait(bar, phase, status)) != 0;
+            if (!landed) {
+                // a copy did not complete within the wait's bound (status holds
+                // SDP_ERR_TIMEOUT): give the copies in flight one more bounded wait, leave
+                tma::mbar_wait(bar, phase, nullptr);
+                return false;
+            }
+            phase ^= 1u;
+        } else {
+            for (int r = warp; r < H * H; r += NWARP) {
+                const int h1 = r / H, h2 = r - h1 * H;
+                const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
+                float2* dst = sg + r * ROW;
+                for (int c = lane; c < ROW; c += 32) {
+                    const int h3 = c / NK, k = c - h3 * NK;
+                    cp_async8(dst + c, src + wrap1(lo3 + h3, M3) * NK + k);
+                }
+            }
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        for (int q = warp; 2 * q < count; q += NWARP) {
+            const int si = 2 * q + half;
+            const bool ok = si < count;
+            const long long s = start + (ok ? si : 2 * q);   // a second half without a sample repeats the first
+            const float4 p = __ldg(pts + s);
+            const int orig = __float_as_int(p.w);
+            const int t = __ldg(tframe + s);
+            const int d1 = (int)ceilf(p.x - g.halfW) - lo1;
+            const int d2 = (int)ceilf(p.y - g.halfW) - lo2;
+            const int d3 = (int)ceilf(p.z - g.halfW) - lo3;
+            // the window lies in the tile by construction of the plan's order; a sample
+            // outside it would read the wrong points, so it is reported and contributes 0
+            const bool inside = (unsigned)d1 <= kTile && (unsigned)d2 <= kTile && (unsigned)d3 <= kTile;
+            const int e1 = inside ? d1 : 0, e2 = inside ? d2 : 0, e3 = inside ? d3 : 0;
+            const float* ws = wts + s * (3 * W);
+            float w1[W];
+            if constexpr (W == 4) {   // 48 bytes per sample: the axis-1 weights are one aligned 16-byte load
+                const float4 v = __ldg(reinterpret_cast<const float4*>(ws));
+                w1[0] = v.x;
+                w1[1] = v.y;
+                w1[2] = v.z;
+                w1[3] = v.w;
+            } else {
+#pragma unroll
+                for (int a = 0; a < W; ++a) w1[a] = __ldg(ws + a);
+            }
+            float w23 = __ldg(ws + W + a2) * __ldg(ws + 2 * W + a3);
+            w23 = (act && ok && inside) ? w23 : 0.f;
+            const unsigned long long* base =
+                reinterpret_cast<const unsigned long long*>(sg + (e1 * H + e2 + a2) * ROW + (e3 + a3) * NK);
+            unsigned long long acc[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) acc[k] = 0ull;
+#pragma unroll
+            for (int a1 = 0; a1 < W; ++a1) {
+                const unsigned long long wa = pk2(w1[a1], w1[a1]);
+#pragma unroll
+                for (int k = 0; k < NK; ++k) acc[k] = fma2(wa, base[a1 * PLANE + k], acc[k]);
+            }
+            const float2* Vt = V + (long long)t * g.K + k0;
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const float2 v = __ldg(Vt + k);
+                const float2 u = upk2(acc[k]);
+                sx = fmaf(v.x, u.x, sx);
+                sx = fmaf(-v.y, u.y, sx);
+                sy = fmaf(v.x, u.y, sy);
+                sy = fmaf(v.y, u.x, sy);
+            }
+            sx *= w23;
+            sy *= w23;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(kFullI, sx, o);
+                sy += __shfl_xor_sync(kFullI, sy, o);
+            }
+            if (ok && l16 == 0) {
+                if (inside)
+                    put(y + (long long)b * J + orig, sx, sy, accumulate);
+                else
+                    atomicCAS(status, 0, SDP_ERR_BOUNDS);
+            }
+        }
+    }
+    return true;
+}
+
 template <int W, int NK>
 __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const int4* __restrict__ tiles, int ntiles,
                                                                     int nt2, int nt3, const float4* __restrict__ pts,
@@ -65,154 +202,58 @@ __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const
                                                                     float2* __restrict__ y, int accumulate,
                                                                     int* status) {
     using D = TileDims<W, NK>;
-    constexpr int H = D::H, ROW = D::ROW, PLANE = D::PLANE;
-    constexpr int NWARP = kTileThreads / 32;
-    constexpr int HW = W / 2;
-    static_assert(ROW % 2 == 0 && D::SIZE % 2 == 0, "16-byte row pieces, 8-byte aligned mbarrier");
+    static_assert(D::ROW % 2 == 0 && D::SIZE % 2 == 0, "16-byte row pieces, 8-byte aligned mbarrier");
     extern __shared__ __align__(16) float2 sg[];   // [h1][h2][h3][k], then the copies' mbarrier
     uint64_t* bar = reinterpret_cast<uint64_t*>(sg + D::SIZE);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int half = lane >> 4, l16 = lane & 15;
-    const bool act = l16 < W * W;
-    const int a2 = act ? l16 / W : 0, a3 = act ? l16 % W : 0;   // idle lanes repeat tap (0, 0) with zero weight
-    const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
-    const long long Gk = (long long)M1 * M2 * M3 * NK;
-    const long long J = g.J;
     if (threadIdx.x == 0) {
         tma::mbar_init(bar, 1);
         tma::fence_init();
     }
     __syncthreads();
     uint32_t phase = 0;
-    for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-        const int4 td = tiles[it];   // (flattened tile index, first sample, sample count, -) of a work item
-        const int t3 = td.x % nt3, t12 = td.x / nt3;
-        const int t2 = t12 % nt2, t1 = t12 / nt2;
-        const int lo1 = t1 * kTile - HW, lo2 = t2 * kTile - HW, lo3 = t3 * kTile - HW;
-        const int start = td.y, count = td.z;
-        // a row's H points along axis 3 start at p0 and run la points before they wrap
-        // around the grid (la = H unless the tile crosses the grid's end along axis 3)
-        const int p0 = wrap1(lo3, M3);
-        const int la = M3 - p0 < H ? M3 - p0 : H;
-        for (int b = 0; b < B; ++b) {
-            __syncthreads();   // the previous pass's readers are done with sg
-            const float2* gb = grids + (long long)b * Gk;
-            // Bulk copies, one per row piece (one or two pieces per row), where every
-            // piece starts on a 16-byte boundary (p0 NK and la NK even, the grid aligned:
-            // W = 4 tiles always); else cp.async 8 bytes per value.
-            const bool bulk = ((p0 * NK) & 1) == 0 && ((la * NK) & 1) == 0 &&
-                              (reinterpret_cast<unsigned long long>(gb) & 15) == 0;
-            if (bulk) {
-                if (threadIdx.x == 0) tma::mbar_expect_tx(bar, (uint32_t)D::BYTES);
-                __syncthreads();   // the expected bytes are registered before any copy lands
-                for (int r = threadIdx.x; r < H * H; r += kTileThreads) {
-                    const int h1 = r / H, h2 = r - h1 * H;
-                    const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
-                    float2* dst = sg + r * ROW;
-                    tma::bulk_g2s(dst, src + (long long)p0 * NK, (uint32_t)(la * NK * 8), bar);
-                    if (la < H) tma::bulk_g2s(dst + la * NK, src, (uint32_t)((H - la) * NK * 8), bar);
-                }
-                const bool landed = __syncthreads_and(tma::mbar_wait(bar, phase, status));
-                if (!landed) {
-                    // a copy did not complete within the wait's bound (status holds
-                    // SDP_ERR_TIMEOUT): give the copies in flight one more bounded wait, leave
-                    tma::mbar_wait(bar, phase, nullptr);
-                    return;
-                }
-                phase ^= 1u;
-            } else {
-                for (int r = warp; r < H * H; r += NWARP) {
-                    const int h1 = r / H, h2 = r - h1 * H;
-                    const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
-                    float2* dst = sg + r * ROW;
-                    for (int c = lane; c < ROW; c += 32) {
-                        const int h3 = c / NK, k = c - h3 * NK;
-                        cp_async8(dst + c, src + wrap1(lo3 + h3, M3) * NK + k);
-                    }
-                }
-                cp_async_wait_all();
-                __syncthreads();
-            }
-            for (int q = warp; 2 * q < count; q += NWARP) {
-                const int si = 2 * q + half;
-                const bool ok = si < count;
-                const long long s = start + (ok ? si : 2 * q);   // a second half without a sample repeats the first
-                const float4 p = __ldg(pts + s);
-                const int orig = __float_as_int(p.w);
-                const int t = __ldg(tframe + s);
-                const int d1 = (int)ceilf(p.x - g.halfW) - lo1;
-                const int d2 = (int)ceilf(p.y - g.halfW) - lo2;
-                const int d3 = (int)ceilf(p.z - g.halfW) - lo3;
-                // the window lies in the tile by construction of the plan's order; a sample
-                // outside it would read the wrong points, so it is reported and contributes 0
-                const bool inside = (unsigned)d1 <= kTile && (unsigned)d2 <= kTile && (unsigned)d3 <= kTile;
-                const int e1 = inside ? d1 : 0, e2 = inside ? d2 : 0, e3 = inside ? d3 : 0;
-                const float* ws = wts + s * (3 * W);
-                float w1[W];
-                if constexpr (W == 4) {   // 48 bytes per sample: the axis-1 weights are one aligned 16-byte load
-                    const float4 v = __ldg(reinterpret_cast<const float4*>(ws));
-                    w1[0] = v.x;
-                    w1[1] = v.y;
-                    w1[2] = v.z;
-                    w1[3] = v.w;
-                } else {
-#pragma unroll
-                    for (int a = 0; a < W; ++a) w1[a] = __ldg(ws + a);
-                }
-                float w23 = __ldg(ws + W + a2) * __ldg(ws + 2 * W + a3);
-                w23 = (act && ok && inside) ? w23 : 0.f;
-                const unsigned long long* base =
-                    reinterpret_cast<const unsigned long long*>(sg + (e1 * H + e2 + a2) * ROW + (e3 + a3) * NK);
-                unsigned long long acc[NK];
-#pragma unroll
-                for (int k = 0; k < NK; ++k) acc[k] = 0ull;
-#pragma unroll
-                for (int a1 = 0; a1 < W; ++a1) {
-                    const unsigned long long wa = pk2(w1[a1], w1[a1]);
-#pragma unroll
-                    for (int k = 0; k < NK; ++k) acc[k] = fma2(wa, base[a1 * PLANE + k], acc[k]);
-                }
-                const float2* Vt = V + (long long)t * g.K + k0;
-                float sx = 0.f, sy = 0.f;
-#pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    const float2 v = __ldg(Vt + k);
-                    const float2 u = upk2(acc[k]);
-                    sx = fmaf(v.x, u.x, sx);
-                    sx = fmaf(-v.y, u.y, sx);
-                    sy = fmaf(v.x, u.y, sy);
-                    sy = fmaf(v.y, u.x, sy);
-                }
-                sx *= w23;
-                sy *= w23;
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    sx += __shfl_xor_sync(kFullI, sx, o);
-                    sy += __shfl_xor_sync(kFullI, sy, o);
-                }
-                if (ok && l16 == 0) {
-                    if (inside)
-                        put(y + (long long)b * J + orig, sx, sy, accumulate);
-                    else
-                        atomicCAS(status, 0, SDP_ERR_BOUNDS);
-                }
-            }
-        }
-    }
+    for (int it = blockIdx.x; it < ntiles; it += gridDim.x)
+        if (!tile_work<W, NK>(g, tiles[it], nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, sg,
+                              bar, phase))
+            return;
+}
+
+// Several plans in one launch (the batched forward's interpolation): the work
+// items of every item of the batch, u.start holding the prefix sums of the items'
+// work-item counts; each work item runs the single-plan body on its item's plan.
+__device__ __forceinline__ int mv_find_item(const MvUnits& u, long long unit) {
+    int i = 0;
+    while (i + 1 < u.n && unit >= u.start[i + 1]) ++i;
+    return i;
 }
 
 template <int W, int NK>
-cudaError_t launch_tiles_k(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
-                           const int* tframe, const float* wts, const float2* V, const float2* grids, int B, int k0,
-                           float2* y, int accumulate, int* status, cudaStream_t st) {
-    constexpr int bytes = TileDims<W, NK>::SMEM;
-    static std::atomic<int> resident{0};   // CTAs per SM, found once per instantiation
+__global__ void __launch_bounds__(kTileThreads) mv_interp_tiles_kernel(const MvArgs a, const MvUnits u) {
+    using D = TileDims<W, NK>;
+    extern __shared__ __align__(16) float2 sg[];   // [h1][h2][h3][k], then the copies' mbarrier
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sg + D::SIZE);
+    if (threadIdx.x == 0) {
+        tma::mbar_init(bar, 1);
+        tma::fence_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (long long w = blockIdx.x; w < u.start[u.n]; w += gridDim.x) {
+        const int i = mv_find_item(u, w);
+        const MvItem& it = a.it[i];
+        if (!tile_work<W, NK>(it.g, it.itiles[w - u.start[i]], it.nt2, it.nt3, it.pts, it.tframe, it.wts, it.V,
+                              it.bufA, it.B, 0, it.y, 0, it.status, sg, bar, phase))
+            return;
+    }
+}
+
+// Resident CTAs per SM of a tiled kernel, found once per instantiation.
+template <class K>
+cudaError_t tiles_grid(K kernel, int bytes, long long nwork, std::atomic<int>& resident, unsigned& grid) {
     int per_sm = resident.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(interp_tiles_kernel<W, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             bytes);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_tiles_kernel<W, NK>, kTileThreads, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTileThreads, bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         resident.store(per_sm, std::memory_order_relaxed);
@@ -221,7 +262,46 @@ cudaError_t launch_tiles_k(const Geo& g, const int4* tiles, int ntiles, int nt2,
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
                                                   cudaSuccess || nsm < 1)
         return cudaErrorInvalidDevice;
-    const int grid = ntiles < nsm * per_sm ? ntiles : nsm * per_sm;
+    const long long nres = (long long)nsm * per_sm;
+    grid = (unsigned)(nwork < nres ? nwork : nres);
+    return cudaSuccess;
+}
+
+template <int W, int NK>
+cudaError_t launch_mv_tiles_k(const MvArgs& a, const MvUnits& u, cudaStream_t st) {
+    constexpr int bytes = TileDims<W, NK>::SMEM;
+    static std::atomic<int> resident{0};
+    unsigned grid = 0;
+    const cudaError_t e = tiles_grid(mv_interp_tiles_kernel<W, NK>, bytes, u.start[u.n], resident, grid);
+    if (e != cudaSuccess) return e;
+    mv_interp_tiles_kernel<W, NK><<<grid, kTileThreads, bytes, st>>>(a, u);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_mv_tiles_w(const MvArgs& a, const MvUnits& u, int K, cudaStream_t st) {
+    switch (K) {
+        case 1: return launch_mv_tiles_k<W, 1>(a, u, st);
+        case 2: return launch_mv_tiles_k<W, 2>(a, u, st);
+        case 3: return launch_mv_tiles_k<W, 3>(a, u, st);
+        case 4: return launch_mv_tiles_k<W, 4>(a, u, st);
+        case 5: return launch_mv_tiles_k<W, 5>(a, u, st);
+        case 6: return launch_mv_tiles_k<W, 6>(a, u, st);
+        case 7: return launch_mv_tiles_k<W, 7>(a, u, st);
+        case 8: return launch_mv_tiles_k<W, 8>(a, u, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int W, int NK>
+cudaError_t launch_tiles_k(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
+                           const int* tframe, const float* wts, const float2* V, const float2* grids, int B, int k0,
+                           float2* y, int accumulate, int* status, cudaStream_t st) {
+    constexpr int bytes = TileDims<W, NK>::SMEM;
+    static std::atomic<int> resident{0};
+    unsigned grid = 0;
+    const cudaError_t e = tiles_grid(interp_tiles_kernel<W, NK>, bytes, ntiles, resident, grid);
+    if (e != cudaSuccess) return e;
     interp_tiles_kernel<W, NK><<<grid, kTileThreads, bytes, st>>>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V,
                                                                   grids, B, k0, y, accumulate, status);
     return cudaGetLastError();
@@ -249,6 +329,15 @@ cudaError_t launch_tiles_w(const Geo& g, const int4* tiles, int ntiles, int nt2,
 int interp_tile_edge() { return kTile; }
 
 bool interp_tiles_supported(int W, int nk) { return (W == 2 || W == 4) && nk >= 1 && nk <= 8; }
+
+cudaError_t launch_mv_interp_tiles(const MvArgs& a, const MvUnits& u, int W, int K, cudaStream_t st) {
+    if (u.start[u.n] == 0) return cudaSuccess;
+    switch (W) {
+        case 2: return launch_mv_tiles_w<2>(a, u, K, st);
+        case 4: return launch_mv_tiles_w<4>(a, u, K, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_interp_tiles(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
                                 const int* tframe, const float* wts, const float2* V, const float2* grids, int B,

@@ -147,6 +147,25 @@ def test_one_launch_per_stage_for_a_mixed_size_batch():
         assert v["A"].status() == 0
 
 
+def test_tiled_interpolation_batched_equals_single_calls():
+    """Plans with the tiled interpolation, of different grid sizes, share one launch per
+    stage: the batched forward is 4 launches and each item equals its own single call bit
+    for bit (the same per-work-item body runs)."""
+    from paper_2408_02367_gb300 import op
+    tun = {"spread_bins": (4, 4, 4), "spread_chunk": 256, "interp_tiled": 1}
+    vols = [_volume((64, 64, 64), 4, 1.25, 5, 4, 12, 300, 21, tuning=tun),          # grids 80^3,
+            _volume((96, 80, 64), 4, 1.25, 5, 3, 10, 400, 22, tuning=tun),          # 120 x 100 x 80,
+            _volume((64, 128, 76), 4, 1.25, 5, 4, 8, 256, 23, tuning=tun)]         # 80 x 160 x 96
+    coil_sets = [[3, 1], [2, 0, 1], [0]]
+    items = [(A, _t(x), _t(np.array(cs, np.int32)), None) for (A, x), cs in zip(vols, coil_sets)]
+    n0 = op.launch_count()
+    ys = op.forward_batched(items)
+    assert op.launch_count() - n0 == 4
+    for (A, x, c, _), y in zip(items, ys):
+        assert torch.equal(y, A.forward(x, c))
+        assert A.status() == 0
+
+
 @pytest.mark.parametrize("bins", [(8, 4, 8), (4, 4, 4), (4, 4, 8)])
 def test_batched_items_beyond_a_plans_workspace_run_in_waves(bins):
     """Items of one plan whose minibatches exceed its max_batch together run in waves (one launch
