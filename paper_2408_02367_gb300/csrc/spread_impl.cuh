@@ -259,9 +259,29 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
             const int orig = __float_as_int(p.w);
             const int t = __ldg(a.tframe + s);
             const float* ws = a.wts + (long long)s * NW;
+            // the sample's 3W weights (3W floats from a multiple of 3W: 16-byte loads when
+            // 3W is a multiple of 4, 8-byte loads when even)
             float wl[NW];
+            if constexpr (NW % 4 == 0) {
 #pragma unroll
-            for (int q = 0; q < NW; ++q) wl[q] = __ldg(ws + q);
+                for (int q = 0; q < NW; q += 4) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(ws + q));
+                    wl[q] = v.x;
+                    wl[q + 1] = v.y;
+                    wl[q + 2] = v.z;
+                    wl[q + 3] = v.w;
+                }
+            } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+                for (int q = 0; q < NW; q += 2) {
+                    const float2 v = __ldg(reinterpret_cast<const float2*>(ws + q));
+                    wl[q] = v.x;
+                    wl[q + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NW; ++q) wl[q] = __ldg(ws + q);
+            }
             // tap offset of every bin position, wrapped onto the periodic grid:
             // position x takes weight phi_d(a) with a = (lo + x - m0) mod M if a < W
             const int m01 = (int)ceilf(p.x - g.halfW), m02 = (int)ceilf(p.y - g.halfW);
