@@ -184,12 +184,14 @@ def stage_bytes(w, B, M, ninc):
 
 # DRAM bytes (read + write) of one launch of each kernel on the vol128_w4
 # workload (B=2, K=5), from one `ncu --set full` capture each (profiles/),
-# keyed with a hash of the kernel's source file at capture time (and, for the
-# spread, its bin shape): a kernel whose source has changed since reports null.
+# keyed with a hash of the kernel's source file at capture time (and the kernel
+# variant: spread bin shape, tiled interpolation, staged prologue): a kernel
+# whose source has changed since reports null.
 NCU_TRAFFIC = {
-    ("spread", (8, 4, 4)): ("spread_impl.cuh", "4c832e4000ce8fa9", (95.680000 + 285.588480) * 1e6),
-    "fwd_prologue_fft3": ("fft2.cu", "c0674c266053743b", (117.543936 + 153.601536) * 1e6),
-    "adj_ifft3_epilogue": ("fft2.cu", "c0674c266053743b", (243.318528 + 62.533888) * 1e6),
+    ("spread", (4, 4, 4)): ("spread_impl.cuh", "96e6f1d3a2c5f3a8", (55.751936 + 279.158528) * 1e6),
+    ("interp", 1): ("interp_tiles.cu", "67fb64f1acfbc580", (409.893632 + 11.246592) * 1e6),
+    ("fwd_prologue_fft3", 1): ("fft2_staged.cu", "f6ad11c3b56ad45f", (117.908480 + 152.802816) * 1e6),
+    "adj_ifft3_epilogue": ("fft2_impl.cuh", "8dac350d67a58838", (243.319552 + 62.806272) * 1e6),
 }
 
 
@@ -200,9 +202,11 @@ def source_hash(fname):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(stage, workload_name, B, bins=(8, 4, 8)):
-    """ncu DRAM bytes per launch of `stage`, if captured for this workload, bin shape and the current source."""
-    key = (stage, tuple(bins)) if stage == "spread" else stage
+def measured_traffic(stage, workload_name, B, tuning):
+    """ncu DRAM bytes per launch of `stage`, if captured for this workload, the kernel the tuning
+    selects (spread bin shape, tiled interpolation, staged prologue) and the current source."""
+    key = {"spread": ("spread", tuple(tuning["spread_bins"])), "interp": ("interp", int(tuning["interp_tiled"])),
+           "fwd_prologue_fft3": ("fwd_prologue_fft3", int(tuning["fft_staged"]))}.get(stage, stage)
     if workload_name != "vol128_w4" or B != 2 or key not in NCU_TRAFFIC:
         return None
     fname, h, nbytes = NCU_TRAFFIC[key]
@@ -1037,7 +1041,7 @@ def run_native(args):
                        "speedup_vs_graph": plain_ms / graph_ms},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": measured_traffic(dom, w.name, B, A.tuning["spread_bins"]),
+                     "traffic": measured_traffic(dom, w.name, B, A.tuning),
                      "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches_per_step": per_step},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},

@@ -28,15 +28,17 @@ from tests.test_gpu_parity import assert_close
 pytestmark = pytest.mark.gpu
 FP32_BOUND = 2e-5
 
-# Kernel shapes the benchmark's autotuner picks on the 128^3 workload (8 x 4 x 4 spread
-# bins, 8 lines per CTA in the fused axis-3 FFT kernels; the 256- and 1024-thread
-# interpolation CTAs are within 1% of each other, so both are covered).
+# Kernel shapes the benchmark's autotuner picks on the 128^3 workload (4 x 4 x 4 spread
+# bins, the staged prologue, 8 lines per CTA in the fused axis-3 FFT kernels, the tiled
+# interpolation) and on the whole-brain one (the same without the staged prologue), plus
+# the row interpolation with 1024-thread CTAs, runs of two samples and coil blocks of two
+# (the runner-up), and the defaults.
 BENCH_TUNINGS = {
     "default": None,
-    "tuned_i256": {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                   "interp_threads": 256},
-    "tuned_i1024": {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                    "interp_threads": 1024},
+    "tuned_tiled": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                    "fft_staged": 1, "interp_tiled": 1},
+    "tuned_rows": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                   "interp_threads": 1024, "interp_run": 2, "interp_coils": 2},
 }
 
 
@@ -115,7 +117,10 @@ def vol200():
     from paper_2408_02367_gb300 import op
     w = synth.WORKLOADS["vol200_w4"]
     x, S, V, omega, frame = synth.make_problem(w)
-    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8, borrow_maps=False)
+    # the kernel shapes the bench's autotuner picks on this workload at B = 8
+    A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8, borrow_maps=False,
+                         tuning={"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
+                                 "interp_tiled": 1})
     geo = O.Geometry(w.n, w.width, w.oversamp)
     assert A.grid == (250, 250, 200)
     yield w, A, geo, x, S, V, omega, frame
@@ -159,7 +164,8 @@ def test_borrowed_coil_maps_give_the_same_bits(vol200):
     from paper_2408_02367_gb300 import op
     w, A, geo, x, S, V, omega, frame = vol200
     St = _t(S)
-    Ab = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, St, max_batch=8, borrow_maps=True)
+    Ab = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, St, max_batch=8, borrow_maps=True,
+                          tuning=A.tuning)
     assert Ab.info()["total_bytes"] < A.info()["total_bytes"] - St.numel() * 8 + 1
     ci = _t(np.array([3, 17], np.int32))
     xt = _t(x)
