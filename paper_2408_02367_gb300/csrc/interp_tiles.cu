@@ -124,22 +124,14 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
             cp_async_wait_all();
             __syncthreads();
         }
-        for (int q = warp; 2 * q < count; q += NWARP) {
-            const int si = 2 * q + half;
-            const bool ok = si < count;
-            const long long s = start + (ok ? si : 2 * q);   // a second half without a sample repeats the first
-            const float4 p = __ldg(pts + s);
-            const int orig = __float_as_int(p.w);
-            const int t = __ldg(tframe + s);
-            const int d1 = (int)ceilf(p.x - g.halfW) - lo1;
-            const int d2 = (int)ceilf(p.y - g.halfW) - lo2;
-            const int d3 = (int)ceilf(p.z - g.halfW) - lo3;
-            // the window lies in the tile by construction of the plan's order; a sample
-            // outside it would read the wrong points, so it is reported and contributes 0
-            const bool inside = (unsigned)d1 <= kTile && (unsigned)d2 <= kTile && (unsigned)d3 <= kTile;
-            const int e1 = inside ? d1 : 0, e2 = inside ? d2 : 0, e3 = inside ? d3 : 0;
+        // a warp takes the sample pairs q = warp, warp + NWARP, ...; the next pair's
+        // coordinates, frame and weights are loaded while the current pair is interpolated
+        auto fetch = [&](int qq, float4& p, int& t, float (&w1)[W], float& w23) {
+            const int si = 2 * qq + half;
+            const long long s = start + (si < count ? si : 2 * qq);   // a second half without a sample repeats the first
+            p = __ldg(pts + s);
+            t = __ldg(tframe + s);
             const float* ws = wts + s * (3 * W);
-            float w1[W];
             if constexpr (W == 4) {   // 48 bytes per sample: the axis-1 weights are one aligned 16-byte load
                 const float4 v = __ldg(reinterpret_cast<const float4*>(ws));
                 w1[0] = v.x;
@@ -150,7 +142,33 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
 #pragma unroll
                 for (int a = 0; a < W; ++a) w1[a] = __ldg(ws + a);
             }
-            float w23 = __ldg(ws + W + a2) * __ldg(ws + 2 * W + a3);
+            w23 = __ldg(ws + W + a2) * __ldg(ws + 2 * W + a3);
+        };
+        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        int tn = 0;
+        float w1n[W], w23n = 0.f;
+        if (2 * warp < count) fetch(warp, pn, tn, w1n, w23n);
+        for (int q = warp; 2 * q < count; q += NWARP) {
+            const bool ok = 2 * q + half < count;
+            const float4 p = pn;
+            const int t = tn;
+            float w1[W];
+#pragma unroll
+            for (int a = 0; a < W; ++a) w1[a] = w1n[a];
+            float w23 = w23n;
+            if (2 * (q + NWARP) < count) fetch(q + NWARP, pn, tn, w1n, w23n);
+            const float2* Vt = V + (long long)t * g.K + k0;
+            float2 vk[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) vk[k] = __ldg(Vt + k);
+            const int orig = __float_as_int(p.w);
+            const int d1 = (int)ceilf(p.x - g.halfW) - lo1;
+            const int d2 = (int)ceilf(p.y - g.halfW) - lo2;
+            const int d3 = (int)ceilf(p.z - g.halfW) - lo3;
+            // the window lies in the tile by construction of the plan's order; a sample
+            // outside it would read the wrong points, so it is reported and contributes 0
+            const bool inside = (unsigned)d1 <= kTile && (unsigned)d2 <= kTile && (unsigned)d3 <= kTile;
+            const int e1 = inside ? d1 : 0, e2 = inside ? d2 : 0, e3 = inside ? d3 : 0;
             w23 = (act && ok && inside) ? w23 : 0.f;
             const unsigned long long* base =
                 reinterpret_cast<const unsigned long long*>(sg + (e1 * H + e2 + a2) * ROW + (e3 + a3) * NK);
@@ -163,11 +181,10 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
 #pragma unroll
                 for (int k = 0; k < NK; ++k) acc[k] = fma2(wa, base[a1 * PLANE + k], acc[k]);
             }
-            const float2* Vt = V + (long long)t * g.K + k0;
             float sx = 0.f, sy = 0.f;
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
-                const float2 v = __ldg(Vt + k);
+                const float2 v = vk[k];
                 const float2 u = upk2(acc[k]);
                 sx = fmaf(v.x, u.x, sx);
                 sx = fmaf(-v.y, u.y, sx);
