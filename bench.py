@@ -191,7 +191,7 @@ NCU_TRAFFIC = {
     ("spread", (4, 4, 4)): ("spread_impl.cuh", "96e6f1d3a2c5f3a8", (55.751936 + 279.158528) * 1e6),
     ("interp", 1): ("interp_tiles.cu", "67fb64f1acfbc580", (409.893632 + 11.246592) * 1e6),
     ("fwd_prologue_fft3", 1): ("fft2_staged.cu", "f6ad11c3b56ad45f", (117.908480 + 152.802816) * 1e6),
-    "adj_ifft3_epilogue": ("fft2_impl.cuh", "8dac350d67a58838", (243.319552 + 62.806272) * 1e6),
+    ("adj_ifft3_epilogue", 0): ("fft2_impl.cuh", "8dac350d67a58838", (243.319552 + 62.806272) * 1e6),
 }
 
 
@@ -206,7 +206,8 @@ def measured_traffic(stage, workload_name, B, tuning):
     """ncu DRAM bytes per launch of `stage`, if captured for this workload, the kernel the tuning
     selects (spread bin shape, tiled interpolation, staged prologue) and the current source."""
     key = {"spread": ("spread", tuple(tuning["spread_bins"])), "interp": ("interp", int(tuning["interp_tiled"])),
-           "fwd_prologue_fft3": ("fwd_prologue_fft3", int(tuning["fft_staged"]))}.get(stage, stage)
+           "fwd_prologue_fft3": ("fwd_prologue_fft3", int(tuning["fft_staged"]) & 1),
+           "adj_ifft3_epilogue": ("adj_ifft3_epilogue", int(tuning["fft_staged"]) >> 1 & 1)}.get(stage, stage)
     if workload_name != "vol128_w4" or B != 2 or key not in NCU_TRAFFIC:
         return None
     fname, h, nbytes = NCU_TRAFFIC[key]
@@ -446,8 +447,10 @@ WHOLE_BRAIN_REFINE = [
     {"fft_lines": 8, "interp_threads": 1024, "interp_coils": 2},
     {"fft_lines": 8, "interp_threads": 1024, "interp_coils": 2, "interp_run": 2},
     {"fft_lines": 8, "interp_threads": 256, "interp_coils": 2},
-    {"fft_lines": 8, "interp_threads": 1024, "fft_staged": 1},
     {"fft_lines": 8, "interp_tiled": 1},
+    {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 1},
+    {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 2},
+    {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 3},
 ]
 
 

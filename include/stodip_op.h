@@ -164,9 +164,11 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 keeps a large minibatch's working set within L2 and the TLB).
  *   fft_staged    fused axis-3 kernels with their inputs staged by bulk copies
  *                 (cp.async.bulk into double-buffered shared memory, persistent
- *                 CTAs, whole image rows per unit): 0 (default: off) or 1 (on
- *                 where supported: a two-pass length, even N3, 16-byte aligned
- *                 x and S; elsewhere the direct-load kernels run).
+ *                 CTAs, whole image rows per unit), a bit mask: 1 the forward
+ *                 prologue, 2 the adjoint epilogue, 3 both, 0 (default) neither.
+ *                 Where a staged kernel does not apply (a two-pass length, even
+ *                 N3 and 16-byte aligned inputs are needed) the direct-load
+ *                 kernel runs.  Other values: SDP_ERR_INVALID_ARG.
  *   interp_tiled  interpolation from shared-memory tiles: 0 (default: off, the
  *                 row kernel) or 1 (on where supported: W = 2 or 4 and at most 8
  *                 channels per call; elsewhere the row kernel).  The plan orders

@@ -924,7 +924,7 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
             tn->spread_coils < 0 || tn->spread_coils > 2 ||
             (tn->interp_run != 0 && tn->interp_run != 1 && tn->interp_run != 2 && tn->interp_run != 4 &&
              tn->interp_run != 8) ||
-            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch || tn->fft_staged < 0 || tn->fft_staged > 1 ||
+            tn->interp_coils < 0 || tn->interp_coils > kMaxBatch || tn->fft_staged < 0 || tn->fft_staged > 3 ||
             tn->interp_tiled < 0 || tn->interp_tiled > 1)
             return SDP_ERR_INVALID_ARG;
         if (!spread_bins_supported(tn->spread_bins)) return SDP_ERR_UNSUPPORTED;

@@ -399,7 +399,7 @@ cudaError_t launch_fwd_prologue_fft3(const Geo& g, const FftAxis& ax, const floa
                                      const float* dinv2, const float* dinv3, float2* out, int* status,
                                      cudaStream_t st) {
     if (fft2_supported(ax.L) && !g_generic_only && !ax.generic) {
-        if (ax.staged && fft2_prologue_staged_ok(g, ax, x, S, nk))
+        if ((ax.staged & 1) && fft2_prologue_staged_ok(g, ax, x, S, nk))
             return launch_fft2_prologue_staged(g, ax, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, status, st);
         return launch_fft2_fwd_prologue(g, ax, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, status, st);
     }
@@ -417,9 +417,13 @@ cudaError_t launch_adj_fft3_epilogue(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int accumulate,
                                      int* status, cudaStream_t st) {
-    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic)
+    if (fft2_supported(ax.L) && !g_generic_only && !ax.generic) {
+        if ((ax.staged & 2) && fft2_epilogue_staged_ok(g, ax, in, S, nk))
+            return launch_fft2_epilogue_staged(g, ax, in, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out,
+                                               accumulate, status, st);
         return launch_fft2_adj_epilogue(g, ax, in, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out, accumulate,
                                         status, st);
+    }
     const size_t sm = smem_fft_bytes(ax.L) + (size_t)g.N[2] * NLP * sizeof(float2);
     const long long nlines = (long long)g.N[0] * g.N[1] * nk;
     const long long nblk = (nlines + NL - 1) / NL;

@@ -1,6 +1,7 @@
 // Forward prologue + axis-3 FFT (steps A1 and the first pass of A2 of the
 // gridding NUFFT of StoDIP's per-coil operator, Sec. 2 Eq. 1, Sec. 2.1 Eq. 3)
-// with its inputs staged by bulk copies.
+// with its inputs staged by bulk copies; the adjoint's axis-3 FFT + epilogue
+// (A6, A7) in the same form further down.
 //
 // The same arithmetic as fft2_prologue_body (fft2_impl.cuh), organised for
 // the memory system: a unit of work is R whole image rows of one coil and all
@@ -176,6 +177,170 @@ __global__ void __launch_bounds__(kStThreads, (A * B >= 200 ? 2 : 3)) fft2_prolo
     }
 }
 
+// Adjoint axis-3 FFT + epilogue (the last pass of A6 and step A7) with its inputs
+// staged by bulk copies: the same arithmetic as fft2_epilogue_body.  A unit is R
+// whole rows (NL = R nk grid lines) and a step is (unit, coil): the coil's grid
+// lines of the unit, in[b][row0 .. row0 + R)[0 .. L)[kk] (one contiguous run of
+// R L nk values), and its coil-map rows S_c[row0 .. row0 + R)[:] (R N3 values),
+// copied into shared memory by one thread with cp.async.bulk on an mbarrier.
+// The steps are double-buffered like the prologue's units.  Pass 1 (thread =
+// (line, b), line fastest): the length-A inverse DFT of the line's positions
+// B a + b, the twiddles, into Y.  Pass 2 (thread = (line, q1), q1 fastest): the
+// length-B inverse DFT, the crop to N3, conj(S_c) from shared memory, summed over
+// the coils in registers; after a unit's last coil the thread scales by 1/psi_hat
+// and stores, consecutive threads writing consecutive voxels of an image row.
+template <int A, int B>
+size_t staged_epi_smem(int nk, int N3) {
+    constexpr int L = A * B, LP = L + 1;
+    const int R = staged_rows<A, B>(nk);
+    const size_t head = 16 + (size_t)L * 8 + (size_t)R * nk * LP * 8;
+    const size_t head16 = (head + 15) & ~(size_t)15;
+    return head16 + 2 * ((size_t)R * L * nk + (size_t)R * N3) * 8;
+}
+
+template <int A, int B>
+__global__ void __launch_bounds__(kStThreads, (A * B >= 200 ? 2 : 3)) fft2_epilogue_staged_kernel(
+    Geo g, const float2* __restrict__ twg, const float2* __restrict__ in, const float2* __restrict__ S,
+    const int* __restrict__ coil_idx, int Bc, int k0, int nk, const float* __restrict__ d1,
+    const float* __restrict__ d2, const float* __restrict__ d3, float2* __restrict__ out, int accumulate,
+    int* status) {
+    constexpr int L = A * B;
+    constexpr int LP = L + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int R = staged_rows<A, B>(nk);
+    const int NL = R * nk;
+    const int N2 = g.N[1], N3 = g.N[2];
+    const long long nrows = (long long)g.N[0] * N2;
+    const long long nvox = nrows * N3;
+    const int h = N3 / 2;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);                 // [2]
+    float2* tw = reinterpret_cast<float2*>(smem + 16);                  // [L]
+    float2* Y = tw + L;                                                  // [NL][LP]
+    const size_t head = 16 + (size_t)L * 8 + (size_t)NL * LP * 8;
+    float2* buf0 = reinterpret_cast<float2*>(smem + ((head + 15) & ~(size_t)15));
+    const size_t gridn = (size_t)R * L * nk;                            // grid lines, then coil-map rows
+    const size_t bufn = gridn + (size_t)R * N3;
+    const int tid = threadIdx.x;
+    const long long nblk = (nrows + R - 1) / R;
+    const long long myunits = (long long)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long nsteps = myunits * Bc;   // step k: unit blockIdx.x + (k / Bc) gridDim.x, coil k % Bc
+
+    for (int i = tid; i < L; i += blockDim.x) tw[i] = twg[i];
+    if (tid == 0) {
+        tma::mbar_init(bar, 1);
+        tma::mbar_init(bar + 1, 1);
+        tma::fence_init();
+    }
+    __syncthreads();
+
+    // thread 0: copies of step k into buffer s (the grid lines, then the coil map's rows)
+    auto issue = [&](long long k, int s) {
+        const long long row0 = ((long long)blockIdx.x + (k / Bc) * gridDim.x) * R;
+        const int bb = (int)(k % Bc);
+        const int nr = (int)(nrows - row0 < R ? nrows - row0 : R);
+        const int c = coil_idx[bb];
+        const bool cok = c >= 0 && c < g.C;
+        const uint32_t gbytes = (uint32_t)nr * L * nk * 8, sbytes = (uint32_t)nr * N3 * 8;
+        float2* bs = buf0 + s * bufn;
+        tma::mbar_expect_tx(bar + s, gbytes + (cok ? sbytes : 0u));
+        tma::bulk_g2s(bs, in + ((long long)bb * nrows + row0) * L * nk, gbytes, bar + s);
+        if (cok) tma::bulk_g2s(bs + gridn, S + (long long)c * nvox + row0 * N3, sbytes, bar + s);
+    };
+
+    // pass-2 role, fixed across the coils of a unit: line l2, FFT index q1
+    const int q12 = tid % A, l2 = tid / A;
+    const bool p2 = tid < NL * A;
+    const int rr2 = l2 / nk, kk2 = l2 - rr2 * nk;
+    auto ovox = [&](int q2) {   // output voxel of FFT index q1 + A q2 (>= N3 when cropped away)
+        int o = q12 + A * q2 + h;
+        return o >= L ? o - L : o;
+    };
+    float2 acc[B];
+    StaticFor<0, B>::run([&](auto qc) { acc[decltype(qc)::value] = make_float2(0.f, 0.f); });
+
+    if (tid == 0 && nsteps > 0) issue(0, 0);
+    bool pending[2] = {nsteps > 0, false};     // meaningful in thread 0
+    for (long long k = 0; k < nsteps; ++k) {
+        const int s = (int)(k & 1);
+        if (tid == 0 && k + 1 < nsteps) {
+            issue(k + 1, s ^ 1);
+            pending[s ^ 1] = true;
+        }
+        const bool ok = tma::mbar_wait(bar + s, (uint32_t)(k >> 1) & 1u, status);
+        if (tid == 0) pending[s] = !ok;
+        if (!__syncthreads_and(ok)) {
+            // a copy did not land within the limit: let the ones still in flight finish
+            // (bounded) before the shared memory goes away
+            if (tid == 0)
+                for (int q = 0; q < 2; ++q)
+                    if (pending[q]) tma::mbar_wait(bar + q, (uint32_t)((k + (q != s)) >> 1) & 1u, status);
+            __syncthreads();
+            return;
+        }
+        const long long row0 = ((long long)blockIdx.x + (k / Bc) * gridDim.x) * R;
+        const int bb = (int)(k % Bc);
+        const int nr = (int)(nrows - row0 < R ? nrows - row0 : R);
+        const int c = coil_idx[bb];
+        const bool cok = c >= 0 && c < g.C;
+        if (!cok && tid == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
+        const float2* gs = buf0 + s * bufn;
+        const float2* Ss = gs + gridn;
+        if (tid < NL * B) {
+            const int l1 = tid % NL, b1 = tid / NL;
+            const int rr = l1 / nk, kk = l1 - rr * nk;
+            float2 u[A];
+            StaticFor<0, A>::run([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                u[a] = rr < nr ? gs[((size_t)rr * L + B * a + b1) * nk + kk] : make_float2(0.f, 0.f);
+            });
+            RegDft<A, true>::run(u);
+            StaticFor<0, A>::run([&](auto qc) {
+                constexpr int q1 = decltype(qc)::value;
+                Y[l1 * LP + q1 * B + b1] = q1 == 0 ? u[q1] : cmul(u[q1], twiddle(tw, b1 * q1, true));
+            });
+        }
+        __syncthreads();
+        if (p2 && rr2 < nr && cok) {
+            float2 z[B];
+            StaticFor<0, B>::run([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                z[b] = Y[l2 * LP + q12 * B + b];
+            });
+            RegDft<B, true>::run(z);
+            const float2* Sr = Ss + (size_t)rr2 * N3;
+            StaticFor<0, B>::run([&](auto qc) {
+                constexpr int q2 = decltype(qc)::value;
+                const int o = ovox(q2);
+                if (o < N3) {
+                    float2 sv = Sr[o];
+                    sv.y = -sv.y;
+                    acc[q2] = cadd(acc[q2], cmul(sv, z[q2]));
+                }
+            });
+        }
+        if (bb == Bc - 1) {
+            // the unit's last coil: scale by 1 / psi_hat, store, start the next unit's sums
+            if (p2 && rr2 < nr) {
+                const long long row = row0 + rr2;
+                const int i1 = (int)(row / N2), i2 = (int)(row - (long long)i1 * N2);
+                const float d12 = d1[i1] * d2[i2];
+                float2* dst = out + (long long)(k0 + kk2) * nvox + row * N3;
+                StaticFor<0, B>::run([&](auto qc) {
+                    constexpr int q2 = decltype(qc)::value;
+                    const int o = ovox(q2);
+                    if (o < N3) {
+                        float2 v = cscale(acc[q2], d12 * __ldg(d3 + o));
+                        if (accumulate) v = cadd(v, dst[o]);
+                        dst[o] = v;
+                    }
+                });
+            }
+            StaticFor<0, B>::run([&](auto qc) { acc[decltype(qc)::value] = make_float2(0.f, 0.f); });
+        }
+        __syncthreads();   // Y and buffer s are free for the next pass 1 and step k + 2's copies
+    }
+}
+
 template <class F>
 bool with_len_staged(int L, F&& f) {
     switch (L) {
@@ -243,6 +408,56 @@ cudaError_t launch_fft2_prologue_staged(const Geo& g, const FftAxis& ax, const f
         }
         kern<<<(unsigned)grid, kStThreads, smem, st>>>(g, ax.tw, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out,
                                                         status);
+        err = cudaGetLastError();
+    });
+    return err;
+}
+
+// The staged epilogue needs: a two-pass length, even N3, 16-byte aligned grid and
+// coil maps, one row's channels within a unit, and shared memory for the buffers.
+bool fft2_epilogue_staged_ok(const Geo& g, const FftAxis& ax, const float2* in, const float2* S, int nk) {
+    if (g.N[2] % 2 || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(S) & 15)) return false;
+    bool ok = false;
+    with_len_staged(ax.L, [&](auto sh) {
+        using Sh = decltype(sh);
+        ok = staged_rows<Sh::a, Sh::b>(nk) >= 1 && staged_epi_smem<Sh::a, Sh::b>(nk, g.N[2]) <= 200 * 1024;
+    });
+    return ok;
+}
+
+cudaError_t launch_fft2_epilogue_staged(const Geo& g, const FftAxis& ax, const float2* in, const float2* S,
+                                        const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                        const float* dinv2, const float* dinv3, float2* out, int accumulate,
+                                        int* status, cudaStream_t st) {
+    cudaError_t err = cudaErrorNotSupported;
+    with_len_staged(ax.L, [&](auto sh) {
+        using Sh = decltype(sh);
+        auto kern = fft2_epilogue_staged_kernel<Sh::a, Sh::b>;
+        const size_t smem = staged_epi_smem<Sh::a, Sh::b>(nk, g.N[2]);
+        const int R = staged_rows<Sh::a, Sh::b>(nk);
+        if (R < 1) return;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            err = cudaGetLastError();
+            return;
+        }
+        int per_sm = 0, dev = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            err = cudaErrorInvalidDevice;
+            return;
+        }
+        const long long nrows = (long long)g.N[0] * g.N[1];
+        const long long nunits = (nrows + R - 1) / R;
+        const long long grid = std::min<long long>(nunits, (long long)nsm * per_sm);
+        if (grid < 1) {
+            err = cudaSuccess;
+            return;
+        }
+        kern<<<(unsigned)grid, kStThreads, smem, st>>>(g, ax.tw, in, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out,
+                                                        accumulate, status);
         err = cudaGetLastError();
     });
     return err;

@@ -40,7 +40,7 @@ struct FftAxis {
     int generic;   // 1: always the Stockham kernels (a plan's tuning), 0: two-pass where available
     int lines;     // lines per CTA of the fused axis-3 kernels: 0 = default, 8 or 4
     int cols;      // columns per CTA of the strided axis-1/axis-2 passes: 0 = default, 32 or 8
-    int staged;    // fused axis-3 kernels: 1 = inputs staged by bulk copies where supported
+    int staged;    // fused axis-3 kernels staged by bulk copies where supported: bit 0 prologue, bit 1 epilogue
 };
 
 // A spread subproblem: one chunk of the incidence list of one output bin.
@@ -146,6 +146,12 @@ cudaError_t launch_fft2_fwd_prologue(const Geo& g, const FftAxis& ax, const floa
                                      const int* coil_idx, int B, int k0, int nk, const float* dinv1,
                                      const float* dinv2, const float* dinv3, float2* out, int* status,
                                      cudaStream_t st);
+// Adjoint axis-3 FFT + epilogue with bulk-copy staged inputs (fft2_staged.cu).
+bool fft2_epilogue_staged_ok(const Geo& g, const FftAxis& ax, const float2* in, const float2* S, int nk);
+cudaError_t launch_fft2_epilogue_staged(const Geo& g, const FftAxis& ax, const float2* in, const float2* S,
+                                        const int* coil_idx, int B, int k0, int nk, const float* dinv1,
+                                        const float* dinv2, const float* dinv3, float2* out, int accumulate,
+                                        int* status, cudaStream_t st);
 // Forward prologue + axis-3 FFT with bulk-copy staged inputs (fft2_staged.cu).
 bool fft2_prologue_staged_ok(const Geo& g, const FftAxis& ax, const float2* x, const float2* S, int nk);
 cudaError_t launch_fft2_prologue_staged(const Geo& g, const FftAxis& ax, const float2* x, const float2* S,

@@ -18,7 +18,8 @@ the operator computes, only how fast it runs on a given trajectory and volume:
   their register columns fit, or one);
 - consecutive samples per interpolation warp run, and coils per sweep of the
   interpolation over the samples (all, or two at a time);
-- the forward prologue with its inputs staged by bulk copies, or loaded directly;
+- the forward prologue and the adjoint epilogue with their inputs staged by bulk
+  copies, or loaded directly (each on its own);
 - the interpolation from shared-memory tiles, or the row kernel's gathers.
 
 `autotune` tunes the spread's knobs first and the rest on the fastest spread
@@ -69,10 +70,11 @@ REFINE = [{"fft_lines": 8}, {"fft_lines": 4}, {"fft_lines": 8, "fft_cols": 32}, 
           {"fft_lines": 8, "interp_threads": 256},
           {"fft_lines": 8, "interp_threads": 1024, "interp_run": 1, "interp_coils": 2},
           {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2},
-          {"fft_lines": 8, "fft_staged": 1},
-          {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2, "fft_staged": 1},
-          {"fft_lines": 8, "interp_threads": 256, "interp_run": 1, "interp_coils": 2, "fft_staged": 1},
+          {"fft_lines": 8, "fft_staged": 3},
+          {"fft_lines": 8, "interp_threads": 1024, "interp_run": 2, "interp_coils": 2, "fft_staged": 3},
+          {"fft_lines": 8, "interp_threads": 256, "interp_run": 1, "interp_coils": 2, "fft_staged": 3},
           {"fft_lines": 8, "interp_tiled": 1}, {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 1},
+          {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 2}, {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 3},
           {"fft_engine": 1, "fft_lines": 0}]
 
 

@@ -112,6 +112,12 @@ def test_tuned_plan_rejects_bad_tunings_on_the_host(lib):
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     t = op.Tuning.of({"interp_coils": -1})                                    # 0 .. 64
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"fft_staged": 4})                                       # bit mask of 2 bits
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"interp_tiled": 2})                                     # 0 or 1
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
+    t = op.Tuning.of({"spread_bins": (2, 4, 4)})                               # no kernel for this shape
+    assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 6
     t = op.Tuning.of({})                                                       # valid tuning, no descriptor
     assert lib.sdp_plan_create_tuned(ctypes.byref(h), None, ctypes.byref(t), None) == 1
     assert lib.sdp_plan_tuning(None, ctypes.byref(t)) == 1

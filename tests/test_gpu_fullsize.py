@@ -36,7 +36,7 @@ FP32_BOUND = 2e-5
 BENCH_TUNINGS = {
     "default": None,
     "tuned_tiled": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                    "fft_staged": 1, "interp_tiled": 1},
+                    "fft_staged": 3, "interp_tiled": 1},
     "tuned_rows": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
                    "interp_threads": 1024, "interp_run": 2, "interp_coils": 2},
 }

@@ -174,6 +174,7 @@ def test_generic_fft_engine_matches_oracle(tmp_path):
     {"spread_bins": (4, 4, 8), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8, "interp_threads": 1024},
     {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "interp_tiled": 1},
     {"spread_bins": (8, 4, 8), "spread_chunk": 64, "fft_engine": 0, "interp_tiled": 1, "fft_staged": 1},
+    {"spread_bins": (4, 4, 4), "spread_chunk": 64, "fft_engine": 0, "interp_tiled": 1, "fft_staged": 2},
 ])
 def test_tuned_kernel_shapes_match_oracle(tuning):
     """Every tuning computes the same operator: half-depth spread bins, 4 x 4 bins (two
@@ -414,18 +415,19 @@ def test_autograd_gradient_matches_oracle_adjoint():
                                        ((6, 10, 160), 3, [1]), ((10, 12, 63), 5, [1, 0]),
                                        ((12, 8, 200), 8, [0, 1])])
 def test_staged_prologue_equals_direct_prologue(n, K, coils):
-    """The fused prologue with bulk-copy staged inputs (fft_staged = 1) computes the same forward
-    operator as the direct-load kernel (the same operations per grid line; the compiler may fuse
-    a multiply-add differently, so agreement is to float32 rounding, not bits), on grid lengths
-    160, 80, 200, 250 and with an odd N3 (where the direct kernel runs)."""
+    """The fused axis-3 kernels with bulk-copy staged inputs (fft_staged = 3: the forward prologue
+    and the adjoint epilogue) compute the same operator as the direct-load kernels (the same
+    operations per grid line; the compiler may fuse a multiply-add differently, so agreement is to
+    float32 rounding, not bits), on grid lengths 160, 80, 200, 250 and with an odd N3 (where the
+    direct kernels run)."""
     from paper_2408_02367_gb300 import op
     c = make_case(n, 4, 1.25, K, 2, 12, 1, 300, coils)     # 12 frames: a rank-K subspace for K <= 8
     geo = O.Geometry(c["n"], 4, 1.25)
     base = {"spread_bins": (8, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8}
     A0 = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3, tuning=base)
     A1 = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=3,
-                          tuning=dict(base, fft_staged=1))
-    assert A1.tuning["fft_staged"] == 1
+                          tuning=dict(base, fft_staged=3))
+    assert A1.tuning["fft_staged"] == 3
     x, ci = t(c["x"]), t(c["coils"])
     y0, y1 = A0.forward(x, ci), A1.forward(x, ci)
     assert (torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)).item() < 1e-6
@@ -441,3 +443,14 @@ def test_staged_prologue_equals_direct_prologue(n, K, coils):
     bad = torch.tensor([0, 9], dtype=torch.int32, device="cuda")
     yb = A1.forward(x, bad)
     assert A1.status() == 5 and torch.all(yb[1] == 0)
+    # the adjoint's staged axis-3 FFT + epilogue against the direct kernel and the oracle,
+    # then accumulated into an existing output
+    r = t(synth.random_complex(tuple(y0.shape), 17))
+    a0, a1 = A0.adjoint(r, ci), A1.adjoint(r, ci)
+    assert (torch.linalg.norm(a1 - a0) / torch.linalg.norm(a0)).item() < 1e-6
+    assert_close(a1.cpu().numpy(), O.gridding_adjoint(geo, r.cpu().numpy(), c["S"], c["V"], c["omega"], c["frame"],
+                                                      c["coils"]), FP32_BOUND, f"staged epilogue {n}")
+    acc = a1.clone()
+    A1.adjoint(r, ci, out=acc, accumulate=True)
+    assert (torch.linalg.norm(acc - 2 * a1) / torch.linalg.norm(2 * a1)).item() < 1e-6
+    assert A1.status() == 0
