@@ -17,15 +17,17 @@
 // (cp.async.bulk) per row, two where the row wraps around the grid along axis 3,
 // completing on an mbarrier whose wait is bounded (W = 4; for W = 2 rows that do
 // not start on a 16-byte boundary, cp.async 8 bytes per value), and then
-// interpolates every sample
-// of the tile from shared memory.  The scattered, latency-bound gathers of the
-// row kernel become one coalesced copy per tile and coil plus shared loads.
+// interpolates every sample of the item from shared memory.  The scattered,
+// latency-bound gathers of the row kernel become one coalesced copy per tile
+// and coil plus shared loads.
 //
 // A warp takes two samples at a time, one per half-warp.  Lane (a2, a3) of a
 // half-warp (W^2 <= 16 lanes) owns the axis-2/axis-3 tap pair: over the W
 // axis-1 taps it accumulates phi1(a1) U_k for its tap's nk channels (shared
 // loads at compile-time offsets from one base address), contracts them with
-// V[t, k], scales by phi2(a2) phi3(a3), and the half-warp sums its lanes.
+// V[t, k], scales by phi2(a2) phi3(a3), and the half-warp sums its lanes.  The
+// next pair's coordinates, frame and weights are loaded while the current pair
+// is interpolated.
 // Widths 2 and 4, up to 8 channels per call; other calls use interp.cu.
 #include <atomic>
 
