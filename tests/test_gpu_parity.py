@@ -454,3 +454,10 @@ def test_staged_prologue_equals_direct_prologue(n, K, coils):
     A1.adjoint(r, ci, out=acc, accumulate=True)
     assert (torch.linalg.norm(acc - 2 * a1) / torch.linalg.norm(2 * a1)).item() < 1e-6
     assert A1.status() == 0
+    # an out-of-range coil index in the adjoint: status 5, its term left out of the coil sum
+    r2 = t(synth.random_complex((2, A1.J), 18))
+    for A in (A0, A1):
+        ab = A.adjoint(r2, bad)
+        assert A.status() == 5
+        assert torch.equal(ab, A.adjoint(r2[:1].contiguous(), bad[:1].contiguous()))
+        assert A.status() == 0
