@@ -451,6 +451,8 @@ WHOLE_BRAIN_REFINE = [
     {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 1},
     {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 2},
     {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 3},
+    {"fft_lines": 8, "fft_cols": 8, "interp_tiled": 1, "fft_staged": 2},
+    {"fft_lines": 8, "fft_cols": 32, "interp_tiled": 1, "fft_staged": 2},
 ]
 
 

@@ -75,6 +75,8 @@ REFINE = [{"fft_lines": 8}, {"fft_lines": 4}, {"fft_lines": 8, "fft_cols": 32}, 
           {"fft_lines": 8, "interp_threads": 256, "interp_run": 1, "interp_coils": 2, "fft_staged": 3},
           {"fft_lines": 8, "interp_tiled": 1}, {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 1},
           {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 2}, {"fft_lines": 8, "interp_tiled": 1, "fft_staged": 3},
+          {"fft_lines": 8, "fft_cols": 32, "interp_tiled": 1, "fft_staged": 3},
+          {"fft_lines": 8, "fft_cols": 8, "interp_tiled": 1, "fft_staged": 3},
           {"fft_engine": 1, "fft_lines": 0}]
 
 
