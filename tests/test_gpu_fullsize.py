@@ -29,14 +29,15 @@ pytestmark = pytest.mark.gpu
 FP32_BOUND = 2e-5
 
 # Kernel shapes the benchmark's autotuner picks on the 128^3 workload (4 x 4 x 4 spread
-# bins, the staged prologue, 8 lines per CTA in the fused axis-3 FFT kernels, the tiled
-# interpolation) and on the whole-brain one (the same without the staged prologue), plus
+# bins, the staged prologue and epilogue, 8 lines per CTA in the fused axis-3 FFT kernels,
+# 32 columns per CTA in the strided passes, the tiled interpolation) and on the whole-brain
+# one (the staged epilogue only, 16 columns), plus
 # the row interpolation with 1024-thread CTAs, runs of two samples and coil blocks of two
 # (the runner-up), and the defaults.
 BENCH_TUNINGS = {
     "default": None,
     "tuned_tiled": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                    "fft_staged": 3, "interp_tiled": 1},
+                    "fft_cols": 32, "fft_staged": 3, "interp_tiled": 1},
     "tuned_rows": {"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
                    "interp_threads": 1024, "interp_run": 2, "interp_coils": 2},
 }
@@ -120,7 +121,7 @@ def vol200():
     # the kernel shapes the bench's autotuner picks on this workload at B = 8
     A = op.make_operator(omega, frame, w.n, w.width, w.oversamp, V, S, max_batch=8, borrow_maps=False,
                          tuning={"spread_bins": (4, 4, 4), "spread_chunk": 512, "fft_engine": 0, "fft_lines": 8,
-                                 "interp_tiled": 1})
+                                 "fft_staged": 2, "interp_tiled": 1})
     geo = O.Geometry(w.n, w.width, w.oversamp)
     assert A.grid == (250, 250, 200)
     yield w, A, geo, x, S, V, omega, frame
