@@ -416,6 +416,20 @@ size_t sdp_workspace_bytes(sdp_plan_t plan);
  */
 size_t sdp_workspace_bytes_for(sdp_plan_t plan, int32_t maxB);
 
+/*
+ * Test hook for the bounded waits of the tiled interpolation (interp_tiled;
+ * the paper has no counterpart).  While withhold_row >= 0, every later forward
+ * of this plan that runs the tiled kernel has its first CTA not copy row
+ * withhold_row (0 .. (8 + W)^2 - 1) of its first tile for the first coil: that
+ * CTA's wait for the tile runs out after timeout_ns (0: the default of one
+ * second; else 1e3 .. 1e10 ns), it records SDP_ERR_TIMEOUT in the status word,
+ * waits once more (bounded) and leaves, and the forward's output is not valid.
+ * withhold_row = -1 turns the hook off (the limit stays).  Nothing faults or
+ * hangs: this exercises the timeout path on the device.  SDP_ERR_INVALID_ARG
+ * for a NULL plan or a value out of range.
+ */
+int sdp_plan_set_wait_test(sdp_plan_t plan, int32_t withhold_row, int64_t timeout_ns);
+
 /* Kernels launched by this library in this process so far (all plans). */
 int64_t sdp_launch_count(void);
 

@@ -51,6 +51,8 @@ struct sdp_plan_s {
     int interp_tiled = 0;     // 1: the tiled interpolation where it has a kernel (interp_tiles.cu)
     int nt[3] = {0, 0, 0};    // interpolation tiles per axis
     int n_itiles = 0;         // tiled interpolation work items
+    int wait_test_row = -1;   // test hook (sdp_plan_set_wait_test): a tile row the first CTA withholds
+    long long wait_test_ns = 0;   // and the limit of the tiled kernel's waits (0: one second)
     int nbins = 0;
     int nsub = 0;
     long long ninc = 0;
@@ -566,7 +568,7 @@ cudaError_t plan_interp(const sdp_plan_s* p, const float2* grids, int B, int k0,
     const Geo& g = p->geo;
     if (plan_interp_tiled(p, nk))
         return launch_interp_tiles(g, p->itiles, p->n_itiles, p->nt[1], p->nt[2], p->pts, p->tframe, p->wts, p->V,
-                                   grids, B, k0, nk, y, accumulate, p->status, st);
+                                   grids, B, k0, nk, y, accumulate, p->status, p->wait_test_row, p->wait_test_ns, st);
     return launch_interp(g, p->interp_threads, p->interp_run, p->interp_coils, p->pts, p->tframe, p->wts, p->V, grids,
                          B, k0, nk, y, accumulate, st);
 }
@@ -1095,6 +1097,16 @@ size_t sdp_workspace_bytes_for(sdp_plan_t p, int32_t maxB) {
     const size_t gridA = (size_t)std::max<long long>(G, p->n[0] * p->n[1] * p->M[2]);
     const size_t gridB = (size_t)(p->n[0] * p->M[1] * p->M[2]);
     return (gridA + gridB) * (size_t)p->geo.K * (size_t)maxB * sizeof(float2);
+}
+
+int sdp_plan_set_wait_test(sdp_plan_t p, int32_t withhold_row, int64_t timeout_ns) {
+    if (!p) return SDP_ERR_INVALID_ARG;
+    const int H = interp_tile_edge() + p->geo.W;
+    if (withhold_row < -1 || withhold_row >= H * H) return SDP_ERR_INVALID_ARG;
+    if (timeout_ns != 0 && (timeout_ns < 1000 || timeout_ns > 10000000000LL)) return SDP_ERR_INVALID_ARG;
+    p->wait_test_row = withhold_row;
+    p->wait_test_ns = timeout_ns;
+    return SDP_OK;
 }
 
 int64_t sdp_launch_count(void) { return g_launches.load(); }

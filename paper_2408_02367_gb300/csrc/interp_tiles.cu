@@ -67,7 +67,8 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
                                           const float4* __restrict__ pts, const int* __restrict__ tframe,
                                           const float* __restrict__ wts, const float2* __restrict__ V,
                                           const float2* __restrict__ grids, int B, int k0, float2* __restrict__ y,
-                                          int accumulate, int* status, float2* sg, uint64_t* bar, uint32_t& phase) {
+                                          int accumulate, int* status, float2* sg, uint64_t* bar, uint32_t& phase,
+                                          int withhold_row, unsigned long long wait_ns) {
     using D = TileDims<W, NK>;
     constexpr int H = D::H, ROW = D::ROW, PLANE = D::PLANE;
     constexpr int NWARP = kTileThreads / 32;
@@ -99,17 +100,18 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
             if (threadIdx.x == 0) tma::mbar_expect_tx(bar, (uint32_t)D::BYTES);
             __syncthreads();   // the expected bytes are registered before any copy lands
             for (int r = threadIdx.x; r < H * H; r += kTileThreads) {
+                if (b == 0 && r == withhold_row) continue;   // the wait test hook: this row never lands
                 const int h1 = r / H, h2 = r - h1 * H;
                 const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
                 float2* dst = sg + r * ROW;
                 tma::bulk_g2s(dst, src + (long long)p0 * NK, (uint32_t)(la * NK * 8), bar);
                 if (la < H) tma::bulk_g2s(dst + la * NK, src, (uint32_t)((H - la) * NK * 8), bar);
             }
-            const bool landed = __syncthreads_and(tma::mbar_wait(bar, phase, status)) != 0;
+            const bool landed = __syncthreads_and(tma::mbar_wait(bar, phase, status, wait_ns)) != 0;
             if (!landed) {
                 // a copy did not complete within the wait's bound (status holds
                 // SDP_ERR_TIMEOUT): give the copies in flight one more bounded wait, leave
-                tma::mbar_wait(bar, phase, nullptr);
+                tma::mbar_wait(bar, phase, nullptr, wait_ns);
                 return false;
             }
             phase ^= 1u;
@@ -219,7 +221,8 @@ __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const
                                                                     const float2* __restrict__ V,
                                                                     const float2* __restrict__ grids, int B, int k0,
                                                                     float2* __restrict__ y, int accumulate,
-                                                                    int* status) {
+                                                                    int* status, int withhold_row,
+                                                                    unsigned long long wait_ns) {
     using D = TileDims<W, NK>;
     static_assert(D::ROW % 2 == 0 && D::SIZE % 2 == 0, "16-byte row pieces, 8-byte aligned mbarrier");
     extern __shared__ __align__(16) float2 sg[];   // [h1][h2][h3][k], then the copies' mbarrier
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const
     uint32_t phase = 0;
     for (int it = blockIdx.x; it < ntiles; it += gridDim.x)
         if (!tile_work<W, NK>(g, tiles[it], nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, sg,
-                              bar, phase))
+                              bar, phase, it == 0 ? withhold_row : -1, wait_ns))
             return;
 }
 
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kTileThreads) mv_interp_tiles_kernel(const MvA
         const int i = mv_find_item(u, w);
         const MvItem& it = a.it[i];
         if (!tile_work<W, NK>(it.g, it.itiles[w - u.start[i]], it.nt2, it.nt3, it.pts, it.tframe, it.wts, it.V,
-                              it.bufA, it.B, 0, it.y, 0, it.status, sg, bar, phase))
+                              it.bufA, it.B, 0, it.y, 0, it.status, sg, bar, phase, -1, tma::kWaitNs))
             return;
     }
 }
@@ -315,30 +318,33 @@ cudaError_t launch_mv_tiles_w(const MvArgs& a, const MvUnits& u, int K, cudaStre
 template <int W, int NK>
 cudaError_t launch_tiles_k(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
                            const int* tframe, const float* wts, const float2* V, const float2* grids, int B, int k0,
-                           float2* y, int accumulate, int* status, cudaStream_t st) {
+                           float2* y, int accumulate, int* status, int withhold_row, unsigned long long wait_ns,
+                           cudaStream_t st) {
     constexpr int bytes = TileDims<W, NK>::SMEM;
     static std::atomic<int> resident{0};
     unsigned grid = 0;
     const cudaError_t e = tiles_grid(interp_tiles_kernel<W, NK>, bytes, ntiles, resident, grid);
     if (e != cudaSuccess) return e;
     interp_tiles_kernel<W, NK><<<grid, kTileThreads, bytes, st>>>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V,
-                                                                  grids, B, k0, y, accumulate, status);
+                                                                  grids, B, k0, y, accumulate, status, withhold_row,
+                                                                  wait_ns);
     return cudaGetLastError();
 }
 
 template <int W>
 cudaError_t launch_tiles_w(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
                            const int* tframe, const float* wts, const float2* V, const float2* grids, int B, int k0,
-                           int nk, float2* y, int accumulate, int* status, cudaStream_t st) {
+                           int nk, float2* y, int accumulate, int* status, int wr, unsigned long long wn,
+                           cudaStream_t st) {
     switch (nk) {
-        case 1: return launch_tiles_k<W, 1>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 2: return launch_tiles_k<W, 2>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 3: return launch_tiles_k<W, 3>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 4: return launch_tiles_k<W, 4>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 5: return launch_tiles_k<W, 5>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 6: return launch_tiles_k<W, 6>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 7: return launch_tiles_k<W, 7>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
-        case 8: return launch_tiles_k<W, 8>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, st);
+        case 1: return launch_tiles_k<W, 1>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 2: return launch_tiles_k<W, 2>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 3: return launch_tiles_k<W, 3>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 4: return launch_tiles_k<W, 4>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 5: return launch_tiles_k<W, 5>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 6: return launch_tiles_k<W, 6>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 7: return launch_tiles_k<W, 7>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
+        case 8: return launch_tiles_k<W, 8>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, wr, wn, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -360,11 +366,14 @@ cudaError_t launch_mv_interp_tiles(const MvArgs& a, const MvUnits& u, int W, int
 
 cudaError_t launch_interp_tiles(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
                                 const int* tframe, const float* wts, const float2* V, const float2* grids, int B,
-                                int k0, int nk, float2* y, int accumulate, int* status, cudaStream_t st) {
+                                int k0, int nk, float2* y, int accumulate, int* status, int withhold_row,
+                                long long wait_ns, cudaStream_t st) {
+    const int wr = withhold_row;
+    const unsigned long long wn = wait_ns > 0 ? (unsigned long long)wait_ns : tma::kWaitNs;
     if (ntiles == 0 || B == 0) return cudaSuccess;
     switch (g.W) {
-        case 2: return launch_tiles_w<2>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, status, st);
-        case 4: return launch_tiles_w<4>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, status, st);
+        case 2: return launch_tiles_w<2>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, status, wr, wn, st);
+        case 4: return launch_tiles_w<4>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, nk, y, accumulate, status, wr, wn, st);
         default: return cudaErrorInvalidValue;
     }
 }

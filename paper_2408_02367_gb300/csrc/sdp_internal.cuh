@@ -120,7 +120,8 @@ int interp_tile_edge();
 bool interp_tiles_supported(int W, int nk);
 cudaError_t launch_interp_tiles(const Geo& g, const int4* tiles, int ntiles, int nt2, int nt3, const float4* pts,
                                 const int* tframe, const float* wts, const float2* V, const float2* grids, int B,
-                                int k0, int nk, float2* y, int accumulate, int* status, cudaStream_t st);
+                                int k0, int nk, float2* y, int accumulate, int* status, int withhold_row,
+                                long long wait_ns, cudaStream_t st);
 cudaError_t launch_interp(const Geo& g, int threads, int run, int cblock, const float4* pts, const int* tframe,
                           const float* wts,
                           const float2* V, const float2* grids, int B, int k0, int nk, float2* y, int accumulate,

@@ -54,13 +54,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-// Wait for the phase of `bar` with parity `parity`; false after kWaitNs (and
+// Wait for the phase of `bar` with parity `parity`; false after limit_ns (and
 // the status word then holds SDP_ERR_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > kWaitNs) {
+        if (gtimer() - t0 > limit_ns) {
             if (status) atomicCAS(status, 0, SDP_ERR_TIMEOUT);
             return false;
         }

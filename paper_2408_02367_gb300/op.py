@@ -148,6 +148,7 @@ EXPORTS = {
     "sdp_plan_beta": (ctypes.c_double, [ctypes.c_void_p]),
     "sdp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "sdp_workspace_bytes_for": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32]),
+    "sdp_plan_set_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "sdp_launch_count": (ctypes.c_int64, []),
     "sdp_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "sdp_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -301,6 +302,12 @@ class SubspaceNufft:
     def workspace_bytes_for(self, max_batch):
         """Workspace a plan of this geometry would hold for minibatches of up to max_batch coils."""
         return int(lib().sdp_workspace_bytes_for(self._h, int(max_batch)))
+
+    def set_wait_test(self, withhold_row, timeout_ns=0):
+        """Test hook of the tiled interpolation's bounded copy waits (include/stodip_op.h,
+        sdp_plan_set_wait_test): withhold_row >= 0 makes the first CTA skip that tile row's
+        copy so its wait runs out; -1 turns it off."""
+        _check(lib().sdp_plan_set_wait_test(self._h, int(withhold_row), int(timeout_ns)), "sdp_plan_set_wait_test")
 
     def launches_per_step(self, B):
         """Kernel launches of one dc_loss forward + backward on B coils (all K channels):

@@ -261,6 +261,32 @@ def test_tiled_interpolation_matches_oracle(n, W, sigma, K, coils):
     assert A.status() == 0
 
 
+def test_tiled_interpolation_bounded_wait_runs_out_then_recovers():
+    """The tiled interpolation's wait for a tile's bulk copies is bounded: with one row of the
+    first CTA's first tile withheld (the test hook) and a 20 ms limit, the forward reports
+    SDP_ERR_TIMEOUT instead of hanging, the device stays usable, and with the hook off the next
+    forward matches the oracle.  Invalid hook arguments are refused on the host."""
+    from paper_2408_02367_gb300 import op
+    c = make_case((40, 36, 44), 4, 1.25, 5, 3, 12, 1, 500, [2, 0])
+    geo = O.Geometry(c["n"], 4, 1.25)
+    A = op.make_operator(c["omega"], c["frame"], c["n"], 4, 1.25, c["V"], c["S"], max_batch=2,
+                         tuning={"interp_tiled": 1})
+    with pytest.raises(op.SdpError):
+        A.set_wait_test(144)                       # rows 0 .. 143 of a 12 x 12 tile face
+    with pytest.raises(op.SdpError):
+        A.set_wait_test(3, timeout_ns=10)          # limit below 1 us
+    x, ci = t(c["x"]), t(c["coils"])
+    A.set_wait_test(5, timeout_ns=20_000_000)
+    A.forward(x, ci)
+    assert A.status() == 4                         # SDP_ERR_TIMEOUT
+    assert float((torch.ones(4, device="cuda") * 2).sum()) == 8.0   # the context still works
+    A.set_wait_test(-1, timeout_ns=0)
+    y = A.forward(x, ci).cpu().numpy()
+    assert A.status() == 0
+    assert_close(y, O.gridding_forward(geo, c["x"], c["S"], c["V"], c["omega"], c["frame"], c["coils"]), FP32_BOUND,
+                 "tiled interpolation after the bounded wait ran out")
+
+
 def test_interp_threads_choice_by_width():
     """1024-thread interpolation CTAs exist for W <= 4 only; wider kernels default to 256."""
     from paper_2408_02367_gb300 import op
