@@ -31,10 +31,13 @@
 namespace sdp {
 namespace {
 
-constexpr int kStThreads = 256;
+// Threads per CTA: 512 for lengths of 200 and more (their units then hold twice the
+// rows, halving the barriers per line; one CTA per SM), 256 below (three per SM).
+template <int A, int B>
+__host__ __device__ constexpr int staged_threads() { return A * B >= 200 ? 512 : 256; }
 
 template <int A, int B>
-__host__ __device__ constexpr int staged_lines() { return kStThreads / (A > B ? A : B); }
+__host__ __device__ constexpr int staged_lines() { return staged_threads<A, B>() / (A > B ? A : B); }
 
 // Rows per unit for nk channels (0 when even one row's channels do not fit).
 template <int A, int B>
@@ -52,7 +55,7 @@ size_t staged_smem(int nk, int N3) {
 }
 
 template <int A, int B>
-__global__ void __launch_bounds__(kStThreads, (A * B >= 200 ? 2 : 3)) fft2_prologue_staged_kernel(
+__global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)) fft2_prologue_staged_kernel(
     Geo g, const float2* __restrict__ twg, const float2* __restrict__ x, const float2* __restrict__ S,
     const int* __restrict__ coil_idx, int Bc, int k0, int nk, const float* __restrict__ d1,
     const float* __restrict__ d2, const float* __restrict__ d3, float2* __restrict__ out, int* status) {
@@ -199,7 +202,7 @@ size_t staged_epi_smem(int nk, int N3) {
 }
 
 template <int A, int B>
-__global__ void __launch_bounds__(kStThreads, (A * B >= 200 ? 2 : 3)) fft2_epilogue_staged_kernel(
+__global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)) fft2_epilogue_staged_kernel(
     Geo g, const float2* __restrict__ twg, const float2* __restrict__ in, const float2* __restrict__ S,
     const int* __restrict__ coil_idx, int Bc, int k0, int nk, const float* __restrict__ d1,
     const float* __restrict__ d2, const float* __restrict__ d3, float2* __restrict__ out, int accumulate,
@@ -391,7 +394,8 @@ cudaError_t launch_fft2_prologue_staged(const Geo& g, const FftAxis& ax, const f
             return;
         }
         int per_sm = 0, dev = 0, nsm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStThreads, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, staged_threads<Sh::a, Sh::b>(), smem) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -406,8 +410,8 @@ cudaError_t launch_fft2_prologue_staged(const Geo& g, const FftAxis& ax, const f
             err = cudaSuccess;
             return;
         }
-        kern<<<(unsigned)grid, kStThreads, smem, st>>>(g, ax.tw, x, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out,
-                                                        status);
+        kern<<<(unsigned)grid, staged_threads<Sh::a, Sh::b>(), smem, st>>>(g, ax.tw, x, S, coil_idx, B, k0, nk, dinv1,
+                                                                           dinv2, dinv3, out, status);
         err = cudaGetLastError();
     });
     return err;
@@ -441,7 +445,8 @@ cudaError_t launch_fft2_epilogue_staged(const Geo& g, const FftAxis& ax, const f
             return;
         }
         int per_sm = 0, dev = 0, nsm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStThreads, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, staged_threads<Sh::a, Sh::b>(), smem) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -456,8 +461,8 @@ cudaError_t launch_fft2_epilogue_staged(const Geo& g, const FftAxis& ax, const f
             err = cudaSuccess;
             return;
         }
-        kern<<<(unsigned)grid, kStThreads, smem, st>>>(g, ax.tw, in, S, coil_idx, B, k0, nk, dinv1, dinv2, dinv3, out,
-                                                        accumulate, status);
+        kern<<<(unsigned)grid, staged_threads<Sh::a, Sh::b>(), smem, st>>>(g, ax.tw, in, S, coil_idx, B, k0, nk, dinv1,
+                                                                           dinv2, dinv3, out, accumulate, status);
         err = cudaGetLastError();
     });
     return err;

@@ -62,7 +62,7 @@ struct TileDims {
 // coil the item's tile is copied into sg (bulk copies completing on bar, or cp.async),
 // then the item's samples are interpolated from it.  False if a copy did not land
 // within the wait's bound (status then holds SDP_ERR_TIMEOUT and the caller leaves).
-template <int W, int NK>
+template <int W, int NK, bool TEST = false>
 __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, int nt3,
                                           const float4* __restrict__ pts, const int* __restrict__ tframe,
                                           const float* __restrict__ wts, const float2* __restrict__ V,
@@ -100,18 +100,19 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
             if (threadIdx.x == 0) tma::mbar_expect_tx(bar, (uint32_t)D::BYTES);
             __syncthreads();   // the expected bytes are registered before any copy lands
             for (int r = threadIdx.x; r < H * H; r += kTileThreads) {
-                if (b == 0 && r == withhold_row) continue;   // the wait test hook: this row never lands
+                if (TEST && b == 0 && r == withhold_row) continue;   // the wait test hook: this row never lands
                 const int h1 = r / H, h2 = r - h1 * H;
                 const float2* src = gb + ((long long)wrap1(lo1 + h1, M1) * M2 + wrap1(lo2 + h2, M2)) * M3 * NK;
                 float2* dst = sg + r * ROW;
                 tma::bulk_g2s(dst, src + (long long)p0 * NK, (uint32_t)(la * NK * 8), bar);
                 if (la < H) tma::bulk_g2s(dst + la * NK, src, (uint32_t)((H - la) * NK * 8), bar);
             }
-            const bool landed = __syncthreads_and(tma::mbar_wait(bar, phase, status, wait_ns)) != 0;
+            const bool landed =
+                __syncthreads_and(tma::mbar_wait(bar, phase, status, TEST ? wait_ns : tma::kWaitNs)) != 0;
             if (!landed) {
                 // a copy did not complete within the wait's bound (status holds
                 // SDP_ERR_TIMEOUT): give the copies in flight one more bounded wait, leave
-                tma::mbar_wait(bar, phase, nullptr, wait_ns);
+                tma::mbar_wait(bar, phase, nullptr, TEST ? wait_ns : tma::kWaitNs);
                 return false;
             }
             phase ^= 1u;
@@ -213,7 +214,9 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
     return true;
 }
 
-template <int W, int NK>
+// TEST: the instantiation that honours the wait test hook (withhold_row, wait_ns);
+// the other ignores both, so the hook costs the production kernel nothing.
+template <int W, int NK, bool TEST>
 __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const int4* __restrict__ tiles, int ntiles,
                                                                     int nt2, int nt3, const float4* __restrict__ pts,
                                                                     const int* __restrict__ tframe,
@@ -234,8 +237,8 @@ __global__ void __launch_bounds__(kTileThreads) interp_tiles_kernel(Geo g, const
     __syncthreads();
     uint32_t phase = 0;
     for (int it = blockIdx.x; it < ntiles; it += gridDim.x)
-        if (!tile_work<W, NK>(g, tiles[it], nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, sg,
-                              bar, phase, it == 0 ? withhold_row : -1, wait_ns))
+        if (!tile_work<W, NK, TEST>(g, tiles[it], nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status,
+                                    sg, bar, phase, it == 0 ? withhold_row : -1, wait_ns))
             return;
 }
 
@@ -323,11 +326,20 @@ cudaError_t launch_tiles_k(const Geo& g, const int4* tiles, int ntiles, int nt2,
     constexpr int bytes = TileDims<W, NK>::SMEM;
     static std::atomic<int> resident{0};
     unsigned grid = 0;
-    const cudaError_t e = tiles_grid(interp_tiles_kernel<W, NK>, bytes, ntiles, resident, grid);
+    const bool test = withhold_row >= 0 || wait_ns != tma::kWaitNs;
+    const cudaError_t e = tiles_grid(interp_tiles_kernel<W, NK, false>, bytes, ntiles, resident, grid);
     if (e != cudaSuccess) return e;
-    interp_tiles_kernel<W, NK><<<grid, kTileThreads, bytes, st>>>(g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V,
-                                                                  grids, B, k0, y, accumulate, status, withhold_row,
-                                                                  wait_ns);
+    if (test) {
+        static std::atomic<int> resident_t{0};
+        unsigned grid_t = 0;
+        const cudaError_t et = tiles_grid(interp_tiles_kernel<W, NK, true>, bytes, ntiles, resident_t, grid_t);
+        if (et != cudaSuccess) return et;
+        interp_tiles_kernel<W, NK, true><<<grid_t, kTileThreads, bytes, st>>>(
+            g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, withhold_row, wait_ns);
+    } else {
+        interp_tiles_kernel<W, NK, false><<<grid, kTileThreads, bytes, st>>>(
+            g, tiles, ntiles, nt2, nt3, pts, tframe, wts, V, grids, B, k0, y, accumulate, status, -1, tma::kWaitNs);
+    }
     return cudaGetLastError();
 }
 
