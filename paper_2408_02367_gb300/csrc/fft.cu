@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "index_map.cuh"
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -241,12 +242,12 @@ __global__ void __launch_bounds__(kThreads) fwd_prologue_fft3_kernel(
         __syncthreads();
         const float2* res = fft_columns<false>(bufa, bufb, tw, ax);
         for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-            const int p = e / NL, l = e - (e / NL) * NL;
+            const imap::LinePos lp = imap::stockham_elem(e, NL);
+            const int p = lp.p, l = lp.l;
             const long long gl = l0 + l;
             if (gl < nlines) {
-                const long long row = gl / nk;
-                const int kk = (int)(gl - row * nk);
-                out[(((long long)b * nrows + row) * L + p) * nk + kk] = res[p * NLP + l];
+                const imap::LineRowChannel rc = imap::line_split(gl, nk);
+                out[imap::line_elem((long long)b * nrows + rc.row, L, p, nk, rc.kk)] = res[p * NLP + l];
             }
         }
         __syncthreads();
@@ -281,13 +282,13 @@ __global__ void __launch_bounds__(kThreads) adj_fft3_epilogue_kernel(
         const bool cok = (c >= 0 && c < g.C);
         if (!cok && threadIdx.x == 0) set_status(status, SDP_ERR_BOUNDS);
         for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-            const int p = e / NL, l = e - (e / NL) * NL;
+            const imap::LinePos lp = imap::stockham_elem(e, NL);
+            const int p = lp.p, l = lp.l;
             const long long gl = l0 + l;
             float2 v = make_float2(0.f, 0.f);
             if (gl < nlines) {
-                const long long row = gl / nk;
-                const int kk = (int)(gl - row * nk);
-                v = in[(((long long)b * nrows + row) * L + p) * nk + kk];
+                const imap::LineRowChannel rc = imap::line_split(gl, nk);
+                v = in[imap::line_elem((long long)b * nrows + rc.row, L, p, nk, rc.kk)];
             }
             bufa[p * NLP + l] = v;
         }

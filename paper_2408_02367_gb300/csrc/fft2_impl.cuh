@@ -30,6 +30,7 @@
 
 #include <utility>
 
+#include "index_map.cuh"
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -326,12 +327,14 @@ __device__ __forceinline__ void fft2_prologue_body(
     if (!cok && tid == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
     __syncthreads();
     if (tid < NLT * B) {
-        const int b1 = tid % B, l1 = tid / B;
+        const imap::LinePos r1 = imap::pos_fastest(tid, B);
+        const int b1 = r1.p, l1 = r1.l;
         const long long gl = l0 + l1;
         float2 u[A];
         if (gl < nlines && cok) {
-            const long long row = gl / nk;
-            const int kk = (int)(gl - row * nk);
+            const imap::LineRowChannel rc = imap::line_split(gl, nk);
+            const long long row = rc.row;
+            const int kk = rc.kk;
             const int i1 = (int)(row / N2), i2 = (int)(row - (long long)i1 * N2);
             const float d12 = d1[i1] * d2[i2];
             const float2* xr = x + (long long)(k0 + kk) * nvox + row * N3;
@@ -354,18 +357,20 @@ __device__ __forceinline__ void fft2_prologue_body(
     }
     __syncthreads();
     if (tid < NLT * A) {
-        const int l2 = tid % NLT, q1 = tid / NLT;
+        const imap::LinePos r2 = imap::line_fastest(tid, NLT);
+        const int l2 = r2.l, q1 = r2.p;
         const long long gl = l0 + l2;
         if (gl < nlines) {
-            const long long row = gl / nk;
-            const int kk = (int)(gl - row * nk);
+            const imap::LineRowChannel rc = imap::line_split(gl, nk);
+            const long long row = rc.row;
+            const int kk = rc.kk;
             float2 z[B];
             StaticFor<0, B>::run([&](auto bc) {
                 constexpr int b = decltype(bc)::value;
                 z[b] = Y[l2 * LP + q1 * B + b];
             });
             RegDft<B, false>::run(z);
-            float2* dst = out + (((long long)bb * nrows + row) * L + q1) * nk + kk;
+            float2* dst = out + imap::line_elem((long long)bb * nrows + row, L, q1, nk, kk);
             const int sq = A * nk;   // outputs q1 + A q2 are A grid points apart
             StaticFor<0, B>::run([&](auto qc) {
                 constexpr int q2 = decltype(qc)::value;
@@ -399,17 +404,20 @@ __device__ __forceinline__ void fft2_epilogue_body(
     const long long nvox = nrows * N3;
     const long long l0 = blk * NLT;
     const int h = N3 / 2;
-    const int l1 = tid % NLT, b1 = tid / NLT;
+    const imap::LinePos r1 = imap::line_fastest(tid, NLT);
+    const int l1 = r1.l, b1 = r1.p;
     const bool p1 = tid < NLT * B;
     const long long gl1 = l0 + l1;
     const bool line1 = p1 && gl1 < nlines;
     long long row1 = 0;
     int kk1 = 0;
     if (line1) {
-        row1 = gl1 / nk;
-        kk1 = (int)(gl1 - row1 * nk);
+        const imap::LineRowChannel rc = imap::line_split(gl1, nk);
+        row1 = rc.row;
+        kk1 = rc.kk;
     }
-    const int q12 = tid % A, l2 = tid / A;
+    const imap::LinePos r2 = imap::pos_fastest(tid, A);
+    const int q12 = r2.p, l2 = r2.l;
     const bool p2 = tid < NLT * A;
     const long long gl2 = l0 + l2;
     const bool line2 = p2 && gl2 < nlines;
@@ -422,8 +430,9 @@ __device__ __forceinline__ void fft2_epilogue_body(
     };
     float2 acc[B];
     if (line2) {
-        row2 = gl2 / nk;
-        kk2 = (int)(gl2 - row2 * nk);
+        const imap::LineRowChannel rc = imap::line_split(gl2, nk);
+        row2 = rc.row;
+        kk2 = rc.kk;
     }
     StaticFor<0, B>::run([&](auto qc) { acc[decltype(qc)::value] = make_float2(0.f, 0.f); });
     __syncthreads();
@@ -433,7 +442,7 @@ __device__ __forceinline__ void fft2_epilogue_body(
         if (!cok && tid == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
         if (p1) {
             float2 u[A];
-            const float2* src = in + (((long long)bb * nrows + row1) * L + b1) * nk + kk1;
+            const float2* src = in + imap::line_elem((long long)bb * nrows + row1, L, b1, nk, kk1);
             const int sa = B * nk;   // FFT positions B a + b1 are B grid points apart
             StaticFor<0, A>::run([&](auto ac) {
                 constexpr int a = decltype(ac)::value;

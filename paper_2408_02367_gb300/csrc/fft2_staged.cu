@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)
         if (!cok && tid == 0 && status) atomicCAS(status, 0, SDP_ERR_BOUNDS);
         const float2* Ss = buf0 + s * bufn;
         if (tid < NL * B) {
-            const int l1 = tid / B, b1 = tid - l1 * B;
-            const int rr = l1 / nk, kk = l1 - rr * nk;
+            const imap::StagedLoad sl = imap::staged_load_role(tid, B, nk);
+            const int l1 = sl.l, rr = sl.rr, kk = sl.kk, b1 = sl.b;
             float2 u[A];
             if (rr < nr && cok) {
                 const long long row = row0 + rr;
@@ -156,9 +156,8 @@ __global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)
         }
         __syncthreads();
         if (tid < NL * A) {
-            const int kk = tid % nk;
-            const int q1 = (tid / nk) % A;
-            const int rr = tid / (nk * A);
+            const imap::StagedStore ss = imap::staged_store_role(tid, A, nk);
+            const int kk = ss.kk, q1 = ss.q1, rr = ss.rr;
             if (rr < nr) {
                 float2 z[B];
                 const int l2 = rr * nk + kk;
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)
                     z[b] = Y[l2 * LP + q1 * B + b];
                 });
                 RegDft<B, false>::run(z);
-                float2* dst = out + (((long long)bb * nrows + row0 + rr) * L + q1) * nk + kk;
+                float2* dst = out + imap::line_elem((long long)bb * nrows + row0 + rr, L, q1, nk, kk);
                 const int sq = A * nk;   // outputs q1 + A q2 are A grid points apart
                 StaticFor<0, B>::run([&](auto qc) {
                     constexpr int q2 = decltype(qc)::value;
@@ -251,9 +250,11 @@ __global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)
     };
 
     // pass-2 role, fixed across the coils of a unit: line l2, FFT index q1
-    const int q12 = tid % A, l2 = tid / A;
+    const imap::LinePos r2 = imap::pos_fastest(tid, A);
+    const int q12 = r2.p, l2 = r2.l;
     const bool p2 = tid < NL * A;
-    const int rr2 = l2 / nk, kk2 = l2 - rr2 * nk;
+    const imap::UnitLine ul2 = imap::unit_line_split(l2, nk);
+    const int rr2 = ul2.rr, kk2 = ul2.kk;
     auto ovox = [&](int q2) {   // output voxel of FFT index q1 + A q2 (>= N3 when cropped away)
         int o = q12 + A * q2 + h;
         return o >= L ? o - L : o;
@@ -289,12 +290,14 @@ __global__ void __launch_bounds__(staged_threads<A, B>(), (A * B >= 200 ? 1 : 3)
         const float2* gs = buf0 + s * bufn;
         const float2* Ss = gs + gridn;
         if (tid < NL * B) {
-            const int l1 = tid % NL, b1 = tid / NL;
-            const int rr = l1 / nk, kk = l1 - rr * nk;
+            const imap::LinePos r1 = imap::line_fastest(tid, NL);
+            const int l1 = r1.l, b1 = r1.p;
+            const imap::UnitLine ul = imap::unit_line_split(l1, nk);
+            const int rr = ul.rr, kk = ul.kk;
             float2 u[A];
             StaticFor<0, A>::run([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                u[a] = rr < nr ? gs[((size_t)rr * L + B * a + b1) * nk + kk] : make_float2(0.f, 0.f);
+                u[a] = rr < nr ? gs[imap::line_elem(rr, L, B * a + b1, nk, kk)] : make_float2(0.f, 0.f);
             });
             RegDft<A, true>::run(u);
             StaticFor<0, A>::run([&](auto qc) {

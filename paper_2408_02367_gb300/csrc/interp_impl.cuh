@@ -9,6 +9,7 @@
 // samples of several plans in one launch.
 #pragma once
 
+#include "index_map.cuh"
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -77,20 +78,11 @@ __device__ __forceinline__ void put(float2* __restrict__ dst, float ax, float ay
 // The lane's fixed role in the row kernel: axis-3 tap a3c and channel kk of a
 // group of cg <= 32 / W channels starting at c0 (idle lanes, a3 >= W, repeat
 // the last active lane's tap and channel with a zero coefficient).
-struct RowLane {
-    int a3c;
-    int kk;
-    bool act;
-};
+using RowLane = imap::RowLane;
 
 template <int W>
 __device__ __forceinline__ RowLane row_lane(int lane, int c0, int cg) {
-    const int a3 = lane / cg, kg = lane - a3 * cg;
-    RowLane r;
-    r.act = a3 < W;
-    r.a3c = r.act ? a3 : W - 1;
-    r.kk = c0 + (r.act ? kg : cg - 1);
-    return r;
+    return imap::row_lane_map(lane, c0, cg, W);
 }
 
 // Step A3 for one sample (grid coordinates and original index p, frame t, this

@@ -32,6 +32,7 @@
 #include <atomic>
 
 #include "batch.cuh"
+#include "index_map.cuh"
 #include "interp_impl.cuh"
 #include "tma.cuh"
 
@@ -75,8 +76,9 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
     constexpr int HW = W / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int half = lane >> 4, l16 = lane & 15;
-    const bool act = l16 < W * W;
-    const int a2 = act ? l16 / W : 0, a3 = act ? l16 % W : 0;   // idle lanes repeat tap (0, 0) with zero weight
+    const imap::TileLane tl = imap::tile_lane_map(l16, W);   // idle lanes repeat tap (0, 0) with zero weight
+    const bool act = tl.act;
+    const int a2 = tl.a2, a3 = tl.a3;
     const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
     const long long Gk = (long long)M1 * M2 * M3 * NK;
     const long long J = g.J;
@@ -176,7 +178,7 @@ __device__ __forceinline__ bool tile_work(const Geo& g, const int4 td, int nt2, 
             const int e1 = inside ? d1 : 0, e2 = inside ? d2 : 0, e3 = inside ? d3 : 0;
             w23 = (act && ok && inside) ? w23 : 0.f;
             const unsigned long long* base =
-                reinterpret_cast<const unsigned long long*>(sg + (e1 * H + e2 + a2) * ROW + (e3 + a3) * NK);
+                reinterpret_cast<const unsigned long long*>(sg + imap::tile_offset(e1, e2, e3, 0, a2, a3, 0, H, NK));
             unsigned long long acc[NK];
 #pragma unroll
             for (int k = 0; k < NK; ++k) acc[k] = 0ull;

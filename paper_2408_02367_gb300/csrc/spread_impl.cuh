@@ -43,6 +43,7 @@
 // memory, so consecutive lanes write consecutive 16-byte pieces of those runs.
 #pragma once
 
+#include "index_map.cuh"
 #include "sdp_internal.cuh"
 
 namespace sdp {
@@ -161,34 +162,32 @@ __device__ __forceinline__ void spread_class(int c, unsigned long long (&acc)[NC
 // c1 < n1, c2 < n2, x3 < x3end.  With all nk channels in this group a column is one
 // contiguous run and the warp writes consecutive 16-byte pieces of the runs (16-byte
 // aligned: M3, lo3 and x3end are even, so a pair never straddles x3end); otherwise
-// (channel groups) 8 bytes at a time.  TS = CQ | 1 is odd, so a quarter-warp's
-// 16-byte accesses to tr hit distinct banks.
+// (channel groups) 8 bytes at a time.  TS = CQ | 1 is odd, so the quarter-warps that
+// move their columns' registers into tr write distinct banks; the reads here meet at
+// most two 16-byte slots per bank (where a column's pad slot is skipped).  The index
+// maps are in index_map.cuh.
 template <int B1, int B3, int NK>
 __device__ __forceinline__ void store_cols(const float4* tr, int ncols, float2* g0, long long cstr, long long cs1,
                                            long long cs2, int n1, int n2, int x3end, int nk, int lane) {
     constexpr int NCOL = B1 * kB2;
-    constexpr int CQ = B3 * NK / 2;
-    constexpr int TS = CQ | 1;
+    constexpr int CQ = imap::spread_cq(B3, NK);
+    constexpr int TS = imap::spread_ts(B3, NK);
     if (NK == nk) {
         const int tot = ncols * CQ;
         for (int e = lane; e < tot; e += 32) {
-            const int cl = e / CQ, j = e - cl * CQ;
-            const int s = cl / NCOL, c = cl % NCOL;
-            const int c1 = c >> 2, c2 = c & 3;
-            if (c1 < n1 && c2 < n2 && 2 * j < x3end * NK)
-                *reinterpret_cast<float4*>(g0 + s * cstr + c1 * cs1 + c2 * cs2 + 2 * j) = tr[cl * TS + j];
+            const imap::SpreadPiece pc = imap::spread_pair_piece(e, CQ, NCOL);
+            if (pc.c1 < n1 && pc.c2 < n2 && 2 * pc.j < x3end * NK)
+                *reinterpret_cast<float4*>(g0 + pc.s * cstr + pc.c1 * cs1 + pc.c2 * cs2 + 2 * pc.j) =
+                    tr[pc.cl * TS + pc.j];
         }
     } else {
         const float2* t2 = reinterpret_cast<const float2*>(tr);
         constexpr int PER = B3 * NK;
         const int tot = ncols * PER;
         for (int e = lane; e < tot; e += 32) {
-            const int cl = e / PER, r = e - cl * PER;
-            const int x3 = r / NK, q = r - x3 * NK;
-            const int s = cl / NCOL, c = cl % NCOL;
-            const int c1 = c >> 2, c2 = c & 3;
-            if (c1 < n1 && c2 < n2 && x3 < x3end)
-                g0[s * cstr + c1 * cs1 + c2 * cs2 + (long long)x3 * nk + q] = t2[cl * TS * 2 + r];
+            const imap::SpreadValue pv = imap::spread_value_piece(e, PER, NK, NCOL);
+            if (pv.c1 < n1 && pv.c2 < n2 && pv.x3 < x3end)
+                g0[pv.s * cstr + pv.c1 * cs1 + pv.c2 * cs2 + (long long)pv.x3 * nk + pv.q] = t2[pv.cl * TS * 2 + pv.r];
         }
     }
 }
@@ -210,8 +209,8 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
     // to an even count so that it is read 16 bytes at a time.
     constexpr int NCK = NC * NK;
     constexpr int NCKP = (NCK + 1) & ~1;
-    constexpr int CQ = B3 * NK / 2;
-    constexpr int TS = CQ | 1;
+    constexpr int CQ = imap::spread_cq(B3, NK);
+    constexpr int TS = imap::spread_ts(B3, NK);
     constexpr int kStage = 32 * B3 * 4 + 32 * NCKP * 8 + 32 * kNPS * 4;
     constexpr int kTrCols = NC * NCOL > 32 ? NC * NCOL : 32;   // every coil's columns of the bin
     constexpr int kTr = kTrCols * TS * 16;
@@ -393,7 +392,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int j = 0; j < CQ; ++j)
-                if (IPW == 1 || (j & 1) == h)
+                if (imap::spread_owns_pair(j, IPW, h))
                     tr[(c * NCOL + col) * TS + j] =
                         pair4(acc[c][(2 * j) / NK][(2 * j) % NK], acc[c][(2 * j + 1) / NK][(2 * j + 1) % NK]);
         __syncwarp();
@@ -412,8 +411,8 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
                 (long long)kofs * BP);
 #pragma unroll
             for (int j = 0; j < CQ; ++j)
-                if (IPW == 1 || j % IPW == h)
-                    part[j * NCOL + col] =
+                if (imap::spread_owns_pair(j, IPW, h))
+                    part[imap::spread_partial_pair(j, col, NCOL)] =
                         pair4(acc[c][(2 * j) / NK][(2 * j) % NK], acc[c][(2 * j + 1) / NK][(2 * j + 1) % NK]);
         }
     }
@@ -430,14 +429,14 @@ __device__ __forceinline__ void spread_body(const SpreadArgs& a, int kofs, int B
         const int npc = min(kTrCols / NCOL, nc - c0);
         __syncwarp();
         for (int e = lane; e < npc * CQ * NCOL; e += 32) {
-            const int c = e % NCOL, cj = e / NCOL;
-            const int s = cj / CQ, j = cj - s * CQ;
+            const imap::SpreadPiece pc = imap::spread_sum_piece(e, CQ, NCOL);
+            const int c = pc.c, s = pc.s, j = pc.j;
             const float4* part0 = reinterpret_cast<const float4*>(
                 a.partials + ((long long)(b0 + c0 + s) * a.slots_per_b + sp.slot) * a.slot_elems +
                 (long long)kofs * BP);
             float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int ch = 0; ch < sp.nchunks; ++ch) {
-                const float4 v = __ldcg(part0 + ch * slot4 + j * NCOL + c);
+                const float4 v = __ldcg(part0 + ch * slot4 + j * NCOL + c);   // pair j of column c, [j][c]
                 sum.x += v.x;
                 sum.y += v.y;
                 sum.z += v.z;
