@@ -183,15 +183,20 @@ def stage_bytes(w, B, M, ninc):
 
 
 # DRAM bytes (read + write) of one launch of each kernel on the vol128_w4
-# workload (B=2, K=5), from one `ncu --set full` capture each (profiles/),
-# keyed with a hash of the kernel's source file at capture time (and the kernel
-# variant: spread bin shape, tiled interpolation, staged prologue): a kernel
-# whose source has changed since reports null.
+# workload (B=2, K=5), from one `ncu --set full` capture of a DIP step
+# (profiles/kernels_vol128_w4.md), keyed with a hash of the kernel's source file
+# at capture time and the kernel variant (spread bin shape, tiled interpolation,
+# staged prologue or epilogue, strided columns per CTA): a kernel whose source has
+# changed since reports null.
 NCU_TRAFFIC = {
-    ("spread", (4, 4, 4)): ("spread_impl.cuh", "96e6f1d3a2c5f3a8", (55.815936 + 279.196672) * 1e6),
-    ("interp", 1): ("interp_tiles.cu", "3b17622f63cf29ab", (369.722368 + 10.945792) * 1e6),
-    ("fwd_prologue_fft3", 1): ("fft2_staged.cu", "9109724c45532a27", (117.910784 + 153.059072) * 1e6),
-    ("adj_ifft3_epilogue", 1): ("fft2_staged.cu", "9109724c45532a27", (246.147072 + 61.748992) * 1e6),
+    ("spread", (4, 4, 4)): ("spread_impl.cuh", "bf009aeec1d9f154", (55.761152 + 279.115520) * 1e6),
+    ("interp", 1): ("interp_tiles.cu", "2650bb20b6abb58c", (370.516992 + 10.980864) * 1e6),
+    ("fwd_prologue_fft3", 1): ("fft2_staged.cu", "6d826d9b6950716f", (117.908992 + 152.950528) * 1e6),
+    ("adj_ifft3_epilogue", 1): ("fft2_staged.cu", "6d826d9b6950716f", (246.183424 + 61.779200) * 1e6),
+    ("fwd_fft2", 32): ("fft2_impl.cuh", "2e882cd182edfd57", (209.750528 + 208.728320) * 1e6),
+    ("fwd_fft1", 32): ("fft2_impl.cuh", "2e882cd182edfd57", (262.183680 + 274.098176) * 1e6),
+    ("adj_ifft1", 32): ("fft2_impl.cuh", "2e882cd182edfd57", (327.721984 + 217.612032) * 1e6),
+    ("adj_ifft2", 32): ("fft2_impl.cuh", "2e882cd182edfd57", (262.177024 + 167.035392) * 1e6),
 }
 
 
@@ -204,10 +209,14 @@ def source_hash(fname):
 
 def measured_traffic(stage, workload_name, B, tuning):
     """ncu DRAM bytes per launch of `stage`, if captured for this workload, the kernel the tuning
-    selects (spread bin shape, tiled interpolation, staged prologue) and the current source."""
+    selects (spread bin shape, tiled interpolation, staged prologue or epilogue, strided columns
+    per CTA) and the current source."""
+    cols = int(tuning.get("fft_cols", 0)) or 16
     key = {"spread": ("spread", tuple(tuning["spread_bins"])), "interp": ("interp", int(tuning["interp_tiled"])),
            "fwd_prologue_fft3": ("fwd_prologue_fft3", int(tuning["fft_staged"]) & 1),
-           "adj_ifft3_epilogue": ("adj_ifft3_epilogue", int(tuning["fft_staged"]) >> 1 & 1)}.get(stage, stage)
+           "adj_ifft3_epilogue": ("adj_ifft3_epilogue", int(tuning["fft_staged"]) >> 1 & 1),
+           "fwd_fft2": ("fwd_fft2", cols), "fwd_fft1": ("fwd_fft1", cols),
+           "adj_ifft1": ("adj_ifft1", cols), "adj_ifft2": ("adj_ifft2", cols)}.get(stage, stage)
     if workload_name != "vol128_w4" or B != 2 or key not in NCU_TRAFFIC:
         return None
     fname, h, nbytes = NCU_TRAFFIC[key]
@@ -516,7 +525,7 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
         torch.cuda.synchronize()
         rel = max(float(torch.linalg.norm(y_p - y_b) / torch.linalg.norm(y_b)),
                   float(torch.linalg.norm(g_p - g_b) / torch.linalg.norm(g_b)),
-                  abs(float(loss_p) - float(loss_b)) / abs(float(loss_b)))
+                  abs(float(loss_p.detach()) - float(loss_b)) / abs(float(loss_b)))
         plain_ms = _events_ms(torch, lambda i: _plain_step(A, torch, x_hat, y_meas, coil_dev[i], w.K), 3, flush)
         model = path_model_bytes(w, B, M)
         stages = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
@@ -1084,6 +1093,17 @@ def run_native(args):
     bytes_per_launch = sb[dom] / per_step
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     step_share = {k: round(v["ms_total"] / sum(s["ms_total"] for s in stages.values()), 4) for k, v in stages.items()}
+    # every stage against the same roofline: algorithmic bytes per launch over its average launch time,
+    # beside the ncu DRAM traffic of one launch where a capture of the current kernel exists
+    stage_roofline = {}
+    for k, v in stages.items():
+        if k not in sb:
+            continue
+        alg = sb[k] / (v["launches"] / args.steps)
+        t_ms = v["ms_total"] / v["launches"]
+        stage_roofline[k] = {"alg_bytes_per_launch": alg, "avg_launch_ms": t_ms,
+                             "achieved_gbs": alg / (t_ms * 1e-3) / 1e9, "frac": alg / (t_ms * 1e-3) / 1e9 / hbm,
+                             "traffic": measured_traffic(k, w.name, B, A.tuning)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1118,6 +1138,7 @@ def run_native(args):
                      "launches_per_step": per_step},
         "stage_ms_per_step": {k: v["ms_total"] / args.steps for k, v in stages.items()},
         "stage_share": step_share,
+        "stage_roofline": stage_roofline,
         "path_model": {"bytes_per_step": model, "frac_of_hbm_bound": (model / (hbm * 1e9)) / (best_ms * 1e-3)},
         "operator_rows": rows,
         "scale_rows": scale,
