@@ -525,7 +525,7 @@ def whole_brain_rows(args, torch, op, dev, tuning, flush, hbm):
         torch.cuda.synchronize()
         rel = max(float(torch.linalg.norm(y_p - y_b) / torch.linalg.norm(y_b)),
                   float(torch.linalg.norm(g_p - g_b) / torch.linalg.norm(g_b)),
-                  abs(float(loss_p.detach()) - float(loss_b)) / abs(float(loss_b)))
+                  abs(float(loss_p.detach()) - float(loss_b.detach())) / abs(float(loss_b.detach())))
         plain_ms = _events_ms(torch, lambda i: _plain_step(A, torch, x_hat, y_meas, coil_dev[i], w.K), 3, flush)
         model = path_model_bytes(w, B, M)
         stages = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
