@@ -78,6 +78,28 @@ def test_bench_byte_model_and_oracle_scaling():
     assert sb["fwd_fft1"] == 8 * 2 * 5 * (128 * 160 * 160 + 160 ** 3)
 
 
+def test_bench_measured_traffic_follows_the_captured_kernel(monkeypatch):
+    """The bench reports a stage's ncu DRAM traffic only for the captured workload, batch and
+    kernel variant, and only while the kernel's source is the captured one."""
+    import bench
+    tuned = {"spread_bins": [4, 4, 4], "interp_tiled": 1, "fft_staged": 3, "fft_cols": 32}
+    captured = {fname: h for fname, h, _ in bench.NCU_TRAFFIC.values()}
+    monkeypatch.setattr(bench, "source_hash", lambda fname: captured[fname])
+    stages = ["spread", "interp", "fwd_prologue_fft3", "adj_ifft3_epilogue", "fwd_fft2", "fwd_fft1", "adj_ifft1",
+              "adj_ifft2"]
+    for st in stages:
+        assert bench.measured_traffic(st, "vol128_w4", 2, tuned) > 0
+    assert bench.measured_traffic("residual_loss", "vol128_w4", 2, tuned) is None
+    for st, change in (("spread", {"spread_bins": [8, 4, 4]}), ("interp", {"interp_tiled": 0}),
+                       ("fwd_prologue_fft3", {"fft_staged": 2}), ("adj_ifft3_epilogue", {"fft_staged": 1}),
+                       ("fwd_fft2", {"fft_cols": 0}), ("adj_ifft1", {"fft_cols": 8})):
+        assert bench.measured_traffic(st, "vol128_w4", 2, dict(tuned, **change)) is None
+    assert bench.measured_traffic("spread", "vol200_w4", 2, tuned) is None
+    assert bench.measured_traffic("spread", "vol128_w4", 4, tuned) is None
+    monkeypatch.setattr(bench, "source_hash", lambda fname: "0" * 16)
+    assert all(bench.measured_traffic(st, "vol128_w4", 2, tuned) is None for st in stages)
+
+
 def test_bench_oracle_pieces_sum_to_the_oracle_step():
     """The CPU baseline splits a step into (coil, channel) pieces of the oracle's own steps; their
     sum over channels is the oracle's gridding forward, and the pool runs whole steps."""
