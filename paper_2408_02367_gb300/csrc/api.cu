@@ -945,6 +945,18 @@ int sdp_plan_create_tuned(sdp_plan_t* out, const sdp_plan_desc* d, const sdp_tun
     if (d->frame_offsets[0] != 0 || d->frame_offsets[d->T] != d->J) return SDP_ERR_INVALID_ARG;
     for (int t = 0; t < d->T; ++t)
         if (d->frame_offsets[t + 1] < d->frame_offsets[t]) return SDP_ERR_INVALID_ARG;
+    // size limits, on the host before any device call: grid lengths up to 2^14, and one coil's
+    // channel-interleaved grid and one image indexed with 32-bit offsets
+    {
+        long long G = 1, nvox = 1;
+        for (int a = 0; a < 3; ++a) {
+            const long long m = grid_len(d->n[a], d->oversamp, d->width);
+            if (m > (1 << 14)) return SDP_ERR_UNSUPPORTED;
+            G *= m;
+            nvox *= d->n[a];
+        }
+        if (G * d->K >= (1LL << 31) || nvox >= (1LL << 31)) return SDP_ERR_UNSUPPORTED;
+    }
     sdp_plan_s* p = new (std::nothrow) sdp_plan_s();
     if (!p) return SDP_ERR_OOM;
     if (cudaGetDevice(&p->dev) != cudaSuccess) {

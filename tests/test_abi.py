@@ -62,6 +62,40 @@ def test_plan_create_rejects_bad_arguments_on_the_host(lib):
     assert lib.sdp_residual_loss_noalloc(None, None, 1, None, 1, 1, None, None, None) == 1
 
 
+def test_plan_create_refuses_oversized_grids_before_any_device_call(lib):
+    """A plan whose per-coil grid would need 64-bit offsets (M1 M2 M3 K >= 2^31) or whose grid
+    length exceeds 2^14 along an axis is refused with SDP_ERR_UNSUPPORTED on the host, before the
+    first CUDA call (so also here, without a GPU) and before anything is read from the trajectory,
+    V or the coil maps; a descriptor within the limits gets past the check to that first call."""
+    import numpy as np
+    from paper_2408_02367_gb300 import op
+    assert [lib.sdp_grid_size(v, 1.25, 4) for v in (1024, 640, 20000)] == [1280, 800, 25000]
+    off = np.array([0, 4], dtype=np.int64)
+    dummy = np.zeros(64, dtype=np.float32)     # never read: stands in for device buffers
+
+    def create(n, K):
+        d = op.PlanDesc()
+        d.n = (ctypes.c_int64 * 3)(*n)
+        d.oversamp, d.width, d.K, d.T, d.C, d.J, d.max_batch, d.flags = 1.25, 4, K, 1, 1, 4, 1, 0
+        d.frame_offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.traj = d.V = d.coil_maps = dummy.ctypes.data
+        h = ctypes.c_void_p(1234)
+        rc = lib.sdp_plan_create(ctypes.byref(h), ctypes.byref(d), None)
+        assert h.value is None
+        return rc
+
+    # M = 1280 per axis with K = 2 (G K = 4.2e9), 800 with K = 5 (G K = 2.56e9), 25000 along one axis
+    for n, K in (((1024, 1024, 1024), 2), ((640, 640, 640), 5), ((20000, 2, 2), 1)):
+        assert create(n, K) == 6
+    # the descriptors below pass the size check and would go on to copy from the stand-in
+    # buffers, so they are only made where there is no device: M = 1280 with K = 1
+    # (G = 2.10e9 < 2^31) and M = 640 with K = 5 (G K = 1.3e9)
+    import torch
+    if not torch.cuda.is_available():
+        assert create((1024, 1024, 1024), 1) == 3     # on to cudaGetDevice, which fails here
+        assert create((512, 512, 512), 5) == 3
+
+
 @pytest.mark.parametrize("n,sigma,W", [(32, 2.0, 6), (128, 1.25, 4), (200, 1.25, 4), (160, 1.25, 4),
                                        (14, 2.0, 6), (3, 2.0, 8), (97, 1.5, 5), (24, 1.0, 4)])
 def test_grid_size_and_beta_agree_with_the_oracle(lib, n, sigma, W):
