@@ -77,8 +77,9 @@ typedef struct sdp_plan_s* sdp_plan_t;
  *   oversamp       grid oversampling sigma in [1, 4]; the grid length along axis d
  *                  is the smallest even 2,3,5-smooth M_d >= max(ceil(sigma N_d), 2W).
  *                  M1 M2 M3 K < 2^31 (the K channel grids of one coil, interleaved
- *                  per grid point, are indexed with 32-bit offsets), else
- *                  SDP_ERR_UNSUPPORTED.
+ *                  per grid point, are indexed with 32-bit offsets), N1 N2 N3 < 2^31
+ *                  and every M_d <= 2^14, else SDP_ERR_UNSUPPORTED, returned on
+ *                  the host before any device call or read of traj, V or coil_maps.
  *   width          Kaiser-Bessel kernel width W in taps, 2..8.
  *   K              subspace rank (channels of x), 1..16.
  *   T              frames (rows of V), >= 1.
@@ -152,7 +153,7 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 two where the doubled register columns fit, i.e. 4-deep bins
  *                 with at most 5 channels per group, else one), 1 or 2 (2 falls
  *                 back to one where it does not fit).  Two coils share one
- *                 staging of each incidence's positions, weights and coverage.
+ *                 staging of each incidence's positions and weights.
  *   interp_run    consecutive bin-sorted samples one interpolation warp takes
  *                 before it jumps ahead by the whole grid of warps: 0 (default:
  *                 1), 1, 2, 4 or 8.  Longer runs let a warp's next sample find
@@ -175,7 +176,8 @@ int sdp_plan_create(sdp_plan_t* out, const sdp_plan_desc* desc, void* stream);
  *                 the samples by tiles of 8^3 grid points either way; the tiled
  *                 kernel copies each tile's grid with its window margin into
  *                 shared memory once per coil and interpolates the tile's samples
- *                 from there.  The batched calls run such plans plan by plan.
+ *                 from there.  The batched calls run tiled plans with the same
+ *                 tile kernel, one launch over the work items of every plan.
  */
 typedef struct {
     int32_t spread_bins[3];
