@@ -1,7 +1,8 @@
 // Interpolation of several plans in one launch (the batched forward's last
 // stage; see batch.cu for the layout of a batched launch and batch_sp.cu for
-// the batched spread).  Kernel widths 4 and 6 only: batches of other widths
-// run plan by plan.
+// the batched spread) for plans that use the row kernel; tiled plans take
+// mv_interp_tiles_kernel (interp_tiles.cu).  Kernel widths 4 and 6 only:
+// batches of other widths run plan by plan.
 #include <algorithm>
 
 #include "batch.cuh"
