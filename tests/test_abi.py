@@ -96,6 +96,37 @@ def test_plan_create_refuses_oversized_grids_before_any_device_call(lib):
         assert create((512, 512, 512), 5) == 3
 
 
+def test_every_autotuner_candidate_passes_the_tuning_checks(lib):
+    """Each tuning the autotuner proposes (both rounds, with every first-round spread shape as the
+    base of the second; the library's lists and the bench's whole-brain lists) gets past the library's host-side tuning checks: with a descriptor inside
+    every limit, plan creation reaches its first CUDA call, which fails here without a device.  (On
+    a machine with a device the descriptor's stand-in buffers would be read, so the test skips.)"""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("the stand-in buffers must not reach a device")
+    from paper_2408_02367_gb300 import op, tune
+    off = np.array([0, 4], dtype=np.int64)
+    dummy = np.zeros(64, dtype=np.float32)
+    d = op.PlanDesc()
+    d.n = (ctypes.c_int64 * 3)(16, 16, 16)
+    d.oversamp, d.width, d.K, d.T, d.C, d.J, d.max_batch, d.flags = 1.25, 4, 5, 1, 1, 4, 2, 0
+    d.frame_offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.traj = d.V = d.coil_maps = dummy.ctypes.data
+    import bench
+    first = tune.candidates(full=True)
+    tunings = first + [t for base in first for t in tune.refinements(dict(tune.DEFAULT, **base))]
+    wb = bench.WHOLE_BRAIN_CANDIDATES
+    tunings += wb + [t for base in wb for t in tune.refinements(dict(tune.DEFAULT, **base),
+                                                                   bench.WHOLE_BRAIN_REFINE)]
+    assert len(tunings) > 100
+    for t in tunings:
+        h = ctypes.c_void_p(1234)
+        tt = op.Tuning.of(t)
+        assert lib.sdp_plan_create_tuned(ctypes.byref(h), ctypes.byref(d), ctypes.byref(tt), None) == 3, t
+        assert h.value is None
+
+
 @pytest.mark.parametrize("n,sigma,W", [(32, 2.0, 6), (128, 1.25, 4), (200, 1.25, 4), (160, 1.25, 4),
                                        (14, 2.0, 6), (3, 2.0, 8), (97, 1.5, 5), (24, 1.0, 4)])
 def test_grid_size_and_beta_agree_with_the_oracle(lib, n, sigma, W):
